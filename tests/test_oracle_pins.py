@@ -1,0 +1,501 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against one of: values the paper prints
+(tests/golden/paper_trellis_facts.json), a brute-force maximum-likelihood
+search, a noiseless channel, re-encoding of the survivor path, textbook
+properties of the codes, or a symmetry of linear codes.  A dropped term, a
+wrong sign, an off-by-one in the frame geometry or a swapped tie rule in the
+oracle fails at least one of them.
+"""
+import heapq
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_13579_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return json.load(fh)
+
+
+K7 = oracle.Code(7, synth.K7_GENS)
+K9 = oracle.Code(9, synth.K9_GENS)
+
+
+# ------------------------------------------------------------ trellis facts
+
+def _branch_out(code, state, u):
+    """alpha_out of the branch (state, u) via the oracle's FSM encoder."""
+    return tuple(int(x) for x in oracle.encode_from(code, state, [u])[0])
+
+
+def _next_state_from_history(K, state, u):
+    """Shift-register definition (Sec. II-A): the state is the previous K-1
+    inputs, most recent first; independent of the oracle's formula."""
+    hist = [(state >> (K - 2 - k)) & 1 for k in range(K - 1)]   # in_{t-1}, in_{t-2}, ...
+    new = [u] + hist[:-1]
+    return sum(b << (K - 2 - k) for k, b in enumerate(new))
+
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+def test_trellis_matches_independent_encoder(code):
+    """Branch outputs of the oracle's FSM equal the convolution encoder's
+    output for the input history that defines the state (Eq. encoder)."""
+    K = code.K
+    for s in range(code.n_states):
+        hist = [(s >> (K - 2 - k)) & 1 for k in range(K - 1)]     # in_{t-1} ..
+        for u in (0, 1):
+            seq = np.array(hist[::-1] + [u], dtype=np.uint8)        # oldest first
+            ref = synth.conv_encode(K, code.gens, seq)[-1]
+            assert _branch_out(code, s, u) == tuple(int(x) for x in ref)
+
+
+def test_generator_binary_reading():
+    g = _golden("paper_trellis_facts.json")["code_k7"]
+    assert [format(x, "b") for x in synth.K7_GENS] == g["gens_binary"]
+    assert [format(x, "o") for x in synth.K7_GENS] == g["gens_octal"]
+
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+def test_theorem1_butterflies(code):
+    """Thm. 1 (Eq. radix2:S): left states 2f, 2f+1 reach exactly f and f+2^(k-2)."""
+    K = code.K
+    for f in range(1 << (K - 2)):
+        reach = {_next_state_from_history(K, i, u) for i in (2 * f, 2 * f + 1) for u in (0, 1)}
+        assert reach == {f, f + (1 << (K - 2))}
+
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+def test_corollary_msb_lsb_generators(code):
+    """Corollary (Eq. radix2:boRelatNot): with MSB = LSB = 1 in every
+    generator, outer branches share an output and inner branches carry its
+    complement."""
+    K = code.K
+    half = 1 << (K - 2)
+    for f in range(half):
+        i0, i1 = 2 * f, 2 * f + 1
+        a00 = _branch_out(code, i0, 0)       # i0 -> j0 (input 0 leads to j0 = f)
+        a11 = _branch_out(code, i1, 1)       # i1 -> j1
+        a01 = _branch_out(code, i0, 1)       # i0 -> j1
+        a10 = _branch_out(code, i1, 0)       # i1 -> j0
+        assert a00 == a11
+        assert a01 == tuple(1 - x for x in a00)
+        assert a10 == tuple(1 - x for x in a00)
+
+
+def test_radix2_theta_classes():
+    """Sec. V-B: for k=7 (171,133), 32 butterflies over 4 distinct Theta, 8 each."""
+    g = _golden("paper_trellis_facts.json")["radix2_theta_classes"]
+    mains = [_branch_out(K7, 2 * f, 0) for f in range(1 << (K7.K - 2))]
+    assert len(mains) == g["n_butterflies"]
+    counts = {}
+    for m in mains:
+        counts[m] = counts.get(m, 0) + 1
+    assert len(counts) == g["n_distinct"]
+    assert set(counts.values()) == {g["per_class"]}
+
+
+def _super_branch(code, i, j):
+    """All two-stage paths i -> m -> j: list of (m, 2*beta output bits)."""
+    K = code.K
+    paths = []
+    for u1 in (0, 1):
+        m = _next_state_from_history(K, i, u1)
+        for u2 in (0, 1):
+            if _next_state_from_history(K, m, u2) == j:
+                paths.append((m, _branch_out(code, i, u1) + _branch_out(code, m, u2)))
+    return paths
+
+
+def _dragonfly_states(K, f):
+    """Eq. radix4:S."""
+    q = 1 << (K - 3)
+    left = [4 * f + y for y in range(4)]
+    right = [f + y * q for y in range(4)]
+    mid = [2 * f, 2 * f + 1, 2 * f + (1 << (K - 2)), 2 * f + (1 << (K - 2)) + 1]
+    return left, mid, right
+
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+def test_radix4_unique_paths(code):
+    """Sec. VII theorem: exactly one two-stage path joins every left and right
+    state of a radix-4 dragonfly, through the middle states of Eq. radix4:S."""
+    K = code.K
+    for f in range(1 << (K - 3)):
+        left, mid, right = _dragonfly_states(K, f)
+        for i in left:
+            for j in right:
+                p = _super_branch(code, i, j)
+                assert len(p) == 1
+                assert p[0][0] in mid
+
+
+def _theta_hat(code, f):
+    left, _, right = _dragonfly_states(code.K, f)
+    return [[_super_branch(code, i, j)[0][1] for i in left] for j in right]   # P_j blocks
+
+
+def test_radix4_theta_hat_distinct():
+    """Sec. VIII-D-1: for k=7 (171,133) all 16 main super-branch outputs differ."""
+    g = _golden("paper_trellis_facts.json")["radix4_theta_hat"]
+    mains = [_theta_hat(K7, f)[0][0] for f in range(1 << (K7.K - 3))]
+    assert len(mains) == g["n_dragonflies"]
+    assert len(set(mains)) == g["n_distinct"]
+
+
+def test_dragonfly_groups():
+    """Sec. VIII-D-2: dragonflies whose P_j blocks are the same sets (up to a
+    common permutation of left states) form exactly DG0..DG3."""
+    g = _golden("paper_trellis_facts.json")["dragonfly_groups"]
+    keys = {}
+    for f in range(16):
+        th = _theta_hat(K7, f)
+        key = tuple(frozenset(block) for block in th)
+        keys.setdefault(key, []).append(f)
+    groups = sorted(sorted(v) for v in keys.values())
+    assert groups == sorted([g["DG0"], g["DG1"], g["DG2"], g["DG3"]])
+    # and one common permutation of left states maps every member onto the first
+    for members in groups:
+        base = _theta_hat(K7, members[0])
+        for f in members[1:]:
+            th = _theta_hat(K7, f)
+            perms = [p for p in itertools.permutations(range(4))
+                     if all([th[j][p[y]] for y in range(4)] == base[j] for j in range(4))]
+            assert perms
+
+
+def test_bit_extract_and_general_state_formula():
+    """Eq. bit example (39 -> 3, 7) and Eq. general:S read with the
+    post-bubble taken as the low rho-x bits of y, checked against the
+    trellis: it reproduces the radix-4 indices of Eq. radix4:S and the
+    dragonfly connectivity for rho = 1, 2, 3."""
+    ex = _golden("paper_trellis_facts.json")["bit_extract_example"]
+
+    def bits(x, b, a):
+        return (x >> a) & ((1 << (b - a)) - 1)
+
+    for b, a, want in ex["cases"]:
+        assert bits(ex["x"], b, a) == want
+
+    def s_general(K, rho, f, x, y):
+        pre = bits(y, rho, rho - x) << (K - x - 1)
+        bub = f << (rho - x)
+        post = bits(y, rho - x, 0)
+        return pre + bub + post
+
+    for K in (5, 7):
+        # rho = 2 matches Eq. radix4:S
+        for f in range(1 << (K - 3)):
+            left, mid, right = _dragonfly_states(K, f)
+            assert [s_general(K, 2, f, 0, y) for y in range(4)] == left
+            assert sorted(s_general(K, 2, f, 1, y) for y in range(4)) == sorted(mid)
+            assert [s_general(K, 2, f, 2, y) for y in range(4)] == right
+        # for every rho, stage x+1 states are exactly the successors of stage x states
+        for rho in (1, 2, 3):
+            for f in range(1 << (K - 1 - rho)):
+                for x in range(rho):
+                    cur = {s_general(K, rho, f, x, y) for y in range(1 << rho)}
+                    nxt = {s_general(K, rho, f, x + 1, y) for y in range(1 << rho)}
+                    succ = {_next_state_from_history(K, s, u) for s in cur for u in (0, 1)}
+                    assert succ == nxt
+
+
+def _free_distance(K, gens):
+    """Smallest Hamming weight of a path leaving state 0 and returning to it
+    (Dijkstra over the shift-register trellis; independent of the oracle)."""
+    NS = 1 << (K - 1)
+
+    def out_weight(s, u):
+        hist = [(s >> (K - 2 - k)) & 1 for k in range(K - 1)]
+        seq = np.array(hist[::-1] + [u], dtype=np.uint8)
+        return int(synth.conv_encode(K, gens, seq)[-1].sum())
+
+    start = _next_state_from_history(K, 0, 1)
+    dist = {start: out_weight(0, 1)}
+    heap = [(dist[start], start)]
+    while heap:
+        d, s = heapq.heappop(heap)
+        if s == 0:
+            return d
+        if d > dist.get(s, 1 << 30):
+            continue
+        for u in (0, 1):
+            t = _next_state_from_history(K, s, u)
+            nd = d + out_weight(s, u)
+            if nd < dist.get(t, 1 << 30):
+                dist[t] = nd
+                heapq.heappush(heap, (nd, t))
+    assert NS > 0
+    return None
+
+
+def test_free_distances_textbook():
+    facts = _golden("code_facts.json")
+    assert _free_distance(7, synth.K7_GENS) == facts["k7_171_133_free_distance"]["value"]
+    assert _free_distance(9, synth.K9_GENS) == facts["k9_557_663_711_free_distance"]["value"]
+
+
+# ------------------------------------------------------------- P1 noiseless
+
+def _noiseless_llr(code, bits, terminated, amp=127):
+    tx = bits if not terminated else np.concatenate([bits, np.zeros(code.K - 1, np.uint8)])
+    c = synth.conv_encode(code.K, code.gens, tx)
+    return (amp * (1 - 2 * c.astype(np.int32))).astype(np.int32)
+
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+@pytest.mark.parametrize("terminated", [False, True])
+def test_noiseless_returns_message(code, terminated):
+    rng = np.random.Generator(np.random.PCG64(12345))
+    n = 3000
+    bits = synth.random_bits(rng, n)
+    llr = _noiseless_llr(code, bits, terminated)
+    want = oracle.pack_bits(bits)
+    assert np.array_equal(oracle.decode_full(code, llr, n, terminated=terminated), want)
+    for f, v in ((256, 42), (96, code.K - 1), (100, 2 * code.K), (64, 0) if not terminated else (64, 7)):
+        got = oracle.decode(code, llr, n, f=f, v=v, terminated=terminated, threads=3)
+        if v < code.K - 1:
+            continue   # with no overlap the frame edges are guesses; checked elsewhere
+        assert np.array_equal(got, want), (f, v)
+    # closed form: the final maximum metric is 127 * beta * T at the true end state
+    path, org, em, im, a = oracle.trace_full(code, llr, n, f=n, v=code.K, s=0, terminated=terminated)
+    T = oracle.n_stages(code, n, terminated)
+    assert em == 127 * code.beta * T
+    assert org == 0 and im == 0
+    assert np.array_equal(path[:n], bits)
+
+
+# --------------------------------------------------------- P2 brute force ML
+
+def _all_messages(n):
+    return ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+
+
+def _batch_encode(K, gens, msgs):
+    n = msgs.shape[1]
+    out = np.zeros((msgs.shape[0], n, len(gens)), dtype=np.uint8)
+    for b, g in enumerate(gens):
+        acc = np.zeros(msgs.shape, dtype=np.int32)
+        for d in range(K):
+            if (g >> (K - 1 - d)) & 1:
+                acc[:, d:] += msgs[:, : n - d]
+        out[:, :, b] = acc & 1
+    return out
+
+
+def _brute_force(code, llr, n, terminated):
+    msgs = _all_messages(n)
+    tx = msgs if not terminated else np.concatenate(
+        [msgs, np.zeros((msgs.shape[0], code.K - 1), np.uint8)], axis=1)
+    cw = _batch_encode(code.K, code.gens, tx)                 # [M, T, beta]
+    corr = ((1 - 2 * cw.astype(np.int64)) * llr[None, :, :].astype(np.int64)).sum(axis=(1, 2))
+    return msgs, corr
+
+
+@pytest.mark.parametrize("K,gens", [(7, synth.K7_GENS), (5, (0o23, 0o35)), (4, (0o13, 0o15, 0o17))])
+@pytest.mark.parametrize("terminated", [False, True])
+@pytest.mark.parametrize("kind", ["random", "erasures", "tiny"])
+def test_brute_force_ml(K, gens, terminated, kind):
+    code = oracle.Code(K, gens)
+    rng = np.random.Generator(np.random.PCG64(777 + K + 10 * terminated))
+    n = 12
+    T = oracle.n_stages(code, n, terminated)
+    for trial in range(6):
+        if kind == "random":
+            llr = rng.integers(-127, 128, size=(T, code.beta)).astype(np.int32)
+        elif kind == "erasures":
+            llr = rng.integers(-127, 128, size=(T, code.beta)).astype(np.int32)
+            llr[rng.random((T, code.beta)) < 0.6] = 0
+        else:
+            llr = rng.integers(-2, 3, size=(T, code.beta)).astype(np.int32)
+        msgs, corr = _brute_force(code, llr, n, terminated)
+        best = corr.max()
+        path, org, em, im, a = oracle.trace_full(code, llr, n, f=n, v=K, s=0, terminated=terminated)
+        assert em == best, (kind, trial)
+        dec = oracle.unpack_bits(oracle.decode_full(code, llr, n, terminated=terminated), n)
+        idx = int((dec.astype(np.int64) << np.arange(n)).sum())
+        assert corr[idx] == best
+        if (corr == best).sum() == 1:
+            assert idx == int(np.argmax(corr))
+
+
+# ------------------------------------------------------------- P3 re-encode
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+@pytest.mark.parametrize("terminated", [False, True])
+def test_reencode_survivor_attains_metric(code, terminated):
+    """Tracing any frame's survivor back to its first stage and re-encoding it
+    from its origin state reproduces end metric - initial metric exactly."""
+    rng = np.random.Generator(np.random.PCG64(99 + code.K))
+    n = 700
+    T = oracle.n_stages(code, n, terminated)
+    llr = rng.integers(-127, 128, size=(T, code.beta)).astype(np.int32)
+    llr[rng.random((T, code.beta)) < 0.3] = 0
+    f, v = 128, 20
+    for s in range(oracle._load().or_num_windows(n, f)):
+        path, org, em, im, a = oracle.trace_full(code, llr, n, f=f, v=v, s=s, terminated=terminated)
+        W = path.size
+        hist = [(org >> k) & 1 for k in range(code.K - 1)]          # oldest first
+        seq = np.concatenate([np.array(hist, np.uint8), path])
+        cw = synth.conv_encode(code.K, code.gens, seq)[code.K - 1:]
+        corr = int(((1 - 2 * cw.astype(np.int64)) * llr[a:a + W].astype(np.int64)).sum())
+        assert corr == em - im, s
+        if a == 0:
+            assert org == 0 and im == 0
+    # full length, terminated: the optimal correlation over all codewords
+    path, org, em, im, a = oracle.trace_full(code, llr, n, f=n, v=code.K, s=0, terminated=terminated)
+    cw = synth.conv_encode(code.K, code.gens, path)
+    assert int(((1 - 2 * cw.astype(np.int64)) * llr.astype(np.int64)).sum()) == em
+
+
+# --------------------------------------------- per-frame brute force (geometry)
+
+def _brute_window(code, llr, n, T, f, v, s, terminated, start_unknown):
+    """ML path over one frame by enumeration, with the frame rules stated in
+    Sec. III (frames of f, v extra stages on each side, clipped) and the
+    start/end rules; returns the decided bits of stages [o, e)."""
+    K = code.K
+    o, e = s * f, min(n, (s + 1) * f)
+    a, b = max(0, o - v), min(T, (s + 1) * f + v)
+    W = b - a
+    starts = [0] if (a == 0 and not start_unknown) else list(range(code.n_states))
+    best, arg = None, None
+    for st in starts:
+        hist = np.array([(st >> k) & 1 for k in range(K - 1)], np.uint8)
+        msgs = _all_messages(W)
+        seqs = np.concatenate([np.repeat(hist[None, :], msgs.shape[0], 0), msgs], axis=1)
+        cw = _batch_encode(K, code.gens, seqs)[:, K - 1:]
+        corr = ((1 - 2 * cw.astype(np.int64)) * llr[a:b][None].astype(np.int64)).sum(axis=(1, 2))
+        if terminated and b == T:
+            endst = np.zeros(msgs.shape[0], dtype=np.int64)
+            for k in range(K - 1):
+                endst |= seqs[:, -1 - k].astype(np.int64) << (K - 2 - k)
+            corr = np.where(endst == 0, corr, np.iinfo(np.int64).min // 2)
+        i = int(np.argmax(corr))
+        if best is None or corr[i] > best:
+            best, arg = corr[i], msgs[i]
+            tie = (corr == corr[i]).sum() > 1
+        elif corr[i] == best:
+            tie = True
+    return arg[o - a:e - a], tie
+
+
+@pytest.mark.parametrize("terminated,start_unknown", [(False, False), (True, False), (False, True)])
+def test_frame_geometry_brute_force(terminated, start_unknown):
+    """Every frame of a segmented decode equals the maximum-likelihood path of
+    that frame alone (no ties: wide-range LLRs), so the frame boundaries,
+    the start rule and the end rule are all pinned."""
+    code = oracle.Code(4, (0o13, 0o15))
+    rng = np.random.Generator(np.random.PCG64(4242 + terminated + 2 * start_unknown))
+    n, f, v = 21, 5, 3
+    T = oracle.n_stages(code, n, terminated)
+    for trial in range(3):
+        llr = rng.integers(-100000, 100001, size=(T, code.beta)).astype(np.int32)
+        got = oracle.unpack_bits(oracle.decode(code, llr, n, f=f, v=v, terminated=terminated,
+                                               start_unknown=start_unknown), n)
+        for s in range(-(-n // f)):
+            want, tie = _brute_window(code, llr, n, T, f, v, s, terminated, start_unknown)
+            if not tie:
+                assert np.array_equal(got[s * f: s * f + want.size], want), (trial, s)
+
+
+# ------------------------------------------------------ tie rules (Alg. 1/2)
+
+def test_tie_rules_on_erased_stream():
+    """With every LLR zero all candidates tie.  Algorithm 1's strict '>'
+    keeps the second predecessor p1 = 2f+1 everywhere and Algorithm 2's
+    argmax takes state 0, so the traceback walks state 0 -> 1 -> 3 -> 7 ...
+    i.e. the decoded input at stage t is bit (k-2) of ((1 << (steps+1)) - 1)."""
+    code = K7
+    n = 40
+    llr = np.zeros((n, 2), np.int32)
+    got = oracle.unpack_bits(oracle.decode_full(code, llr, n), n)
+    # walking back from state 0: states 0, 1, 3, 7, 15, 31, 63, 63, ... so the
+    # decoded bit (MSB of the state after stage t) is 1 for all but the last
+    # K-2+1 stages counted from the end
+    js, want = 0, np.zeros(n, np.uint8)
+    for t in range(n - 1, -1, -1):
+        want[t] = js >> (code.K - 2)
+        js = ((js << 1) & (code.n_states - 1)) | 1
+    assert np.array_equal(got, want)
+    assert got[-1] == 0 and got[0] == 1
+
+
+# ----------------------------------------------------------- P9 symmetry
+
+@pytest.mark.parametrize("code", [K7, K9], ids=["k7", "k9"])
+@pytest.mark.parametrize("f,v", [(10 ** 6, 10), (64, 20)])
+def test_linear_code_symmetry_fp64(code, f, v):
+    """Flipping LLR signs along the codeword of m0 flips the decode by m0
+    (continuous noise, so ties have probability zero)."""
+    rng = np.random.Generator(np.random.PCG64(31337 + code.K))
+    n = 900
+    st = synth.make_stream(rng, code.K, code.gens, n, 2.0, terminated=True)
+    llr = st.f64().reshape(-1, code.beta)
+    m0 = synth.random_bits(rng, n)
+    c0 = synth.conv_encode(code.K, code.gens, np.concatenate([m0, np.zeros(code.K - 1, np.uint8)]))
+    llr2 = llr * (1 - 2 * c0.astype(np.float64))
+    ff = min(f, n)
+    d1, _, _ = oracle.decode_f64(code, llr, n, f=ff, v=v, terminated=True)
+    d2, _, _ = oracle.decode_f64(code, llr2, n, f=ff, v=v, terminated=True)
+    assert np.array_equal(oracle.unpack_bits(d2, n), oracle.unpack_bits(d1, n) ^ m0)
+
+
+def test_f64_matches_i64_on_integer_inputs():
+    """The fp64 oracle equals the int64 oracle on integer LLRs whose decisions
+    are not ties (fp64 sums of small integers are exact)."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = 2000
+    for code in (K7, K9):
+        T = oracle.n_stages(code, n, False)
+        llr = rng.integers(-127, 128, size=(T, code.beta)).astype(np.int32)
+        a = oracle.decode(code, llr, n, f=256, v=42)
+        b, gap, mx = oracle.decode_f64(code, llr.astype(np.float64), n, f=256, v=42)
+        assert np.array_equal(a, b)
+        assert np.all(mx > 0)
+
+
+# ---------------------------------------------------------- P10 BER sanity
+
+def test_ber_falls_with_snr_and_segmentation_costs():
+    n = 1 << 15
+    floor = _golden("paper_trellis_facts.json")["ber_validity"]["factor"] / n
+    full_ber, seg_ber = [], []
+    for ebn0 in (1.0, 2.0, 3.0):
+        st = synth.segmented_stream(ebn0, n_info=n)
+        llr = st.s8().reshape(-1, 2).astype(np.int32)
+        full = oracle.unpack_bits(oracle.decode_full(K7, llr, n), n)
+        seg = oracle.unpack_bits(oracle.decode(K7, llr, n, f=32, v=6, threads=4), n)
+        full_ber.append(np.mean(full != st.bits))
+        seg_ber.append(np.mean(seg != st.bits))
+    assert full_ber[0] > full_ber[1] > full_ber[2]
+    assert full_ber[0] > floor
+    # a short overlap (v = k-1) costs BER at every point
+    for fb, sb in zip(full_ber, seg_ber):
+        assert sb >= fb
+
+
+# ------------------------------------------------------------- depuncture
+
+def test_depuncture_roundtrip():
+    rng = np.random.Generator(np.random.PCG64(8))
+    for pat in (synth.PUNCT_R23, synth.PUNCT_R34):
+        code = oracle.Code(7, synth.K7_GENS, puncture=pat)
+        T = 57
+        full = rng.integers(-127, 128, size=(T, 2)).astype(np.int32)
+        mask = synth.puncture_mask(pat, T)
+        kept = full[mask]
+        assert kept.size == code.n_kept(T)
+        back = oracle.depuncture(code, kept, T)
+        assert np.array_equal(back[mask], full[mask])
+        assert np.all(back[~mask] == 0)
+        with pytest.raises(ValueError):
+            oracle.depuncture(code, kept[:-1], T)
