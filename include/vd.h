@@ -1,0 +1,161 @@
+/*
+ * vd.h — C ABI of the GB300 soft-decision Viterbi decoder (libvd).
+ *
+ * Method: "High-Throughput Parallel Viterbi Decoder on GPU Tensor Cores",
+ * arXiv 2011.13579.  The decoder computes, for a convolutional code of
+ * constraint length k and beta generator polynomials (Sec. II-A, Eq. encoder):
+ *   - branch metrics   delta^{ij}_t = sum_b (-1)^{alpha_out^{ij}[b]} l_t[b]      (Eq. BM)
+ *   - path metrics     lambda^j_t = max_{i in prv(j)} lambda^i_{t-1} + delta^{ij}_t  (Eq. PM)
+ *   - survivors        phi^j_t = argmax of the same                             (Eq. SP0)
+ *   - the forward and backward procedures of Algorithms 1 and 2,
+ *   - over frames of f stages that overlap their neighbours (Sec. III), here
+ *     by v stages on each side,
+ *   - in radix-2 (one stage per step) or radix-4 (two stages per step,
+ *     Sec. VII, Eq. radix4:PM / radix4:SP0) form; both give identical bits.
+ *
+ * Conventions fixed by this library (the paper is silent on them):
+ *   - generators are given as in the paper's octal notation, e.g. 0171, 0133
+ *     for the (2,1,7) code; the most significant of the k bits taps the
+ *     current input;
+ *   - a positive LLR means bit 0 (Sec. II-C); metrics are maximised;
+ *   - ties in the ACS select the odd predecessor 2f+1 (Algorithm 1 keeps the
+ *     first candidate only if it is strictly larger); the final argmax of
+ *     Algorithm 2 takes the lowest state index among equal metrics;
+ *   - frame s decodes stages [s f, min(n_info, (s+1) f)) and runs the trellis
+ *     over [max(0, s f - v), min(T, (s+1) f + v)), T = n_info (+ k-1 when
+ *     terminated).  The frame at stage 0 starts from state 0 unless
+ *     VD_START_UNKNOWN is given; other frames start from all-equal metrics;
+ *     a frame that reaches the end of a terminated stream traces back from
+ *     state 0, others from the best state;
+ *   - decoded bit t is bit (t & 31) of word t >> 5 (LSB-first);
+ *   - received LLRs are time-interleaved: l_t[0..beta-1] for t = 0, 1, ...;
+ *     a punctured code transmits only the kept positions (stage-major, b
+ *     ascending, pattern column t mod period) and the decoder inserts 0 at
+ *     the erased ones.
+ *
+ * Ownership and threading: the caller owns every device buffer it passes and
+ * the stream.  The library owns the vd_code objects and a per-device,
+ * per-stream scratch pool for survivors, which it allocates on first use and
+ * grows as needed (cudaMalloc), and frees in vd_release_scratch() or at
+ * process exit.  Calls on one stream are ordered; calls on different streams
+ * use different scratch buffers.  Launches are asynchronous on the given
+ * stream; errors detected on the host are returned immediately.
+ *
+ * Errors: every function returns a vd_status; no exception, abort or exit
+ * crosses the ABI.  vd_last_error() gives a message for the calling thread's
+ * last failure.
+ */
+#ifndef VD_H
+#define VD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VD_OK = 0,
+    VD_EINVAL = -1,        /* bad argument (message in vd_last_error) */
+    VD_ENOMEM = -2,        /* device or host allocation failed */
+    VD_ECUDA = -3,         /* a CUDA runtime call failed */
+    VD_EUNSUPPORTED = -4,  /* valid request this build has no kernel for */
+    VD_ETIMEOUT = -5,      /* a bounded device wait ran out */
+    VD_EBOUNDS = -6        /* a device-side bounds check fired */
+} vd_status;
+
+/* LLR element types */
+enum { VD_LLR_S8 = 0,      /* int8 in [-127, 127] */
+       VD_LLR_S4 = 1,      /* 4-bit in [-7, 7], two per byte, low nibble = earlier value */
+       VD_LLR_F16 = 2 };   /* IEEE half; metrics in fp32 */
+
+/* flags */
+enum { VD_TERMINATED = 1u,     /* stream ends with k-1 zero tail inputs (state 0) */
+       VD_START_UNKNOWN = 2u,  /* do not assume the encoder starts in state 0 */
+       VD_RETURN_PM = 4u };    /* reserved */
+
+typedef struct vd_code vd_code;   /* opaque, owned by the library */
+
+/* Decoder configuration chosen for one call (by the caller or the tuner). */
+typedef struct vd_tune {
+    int32_t f;         /* frame length (stages decoded per frame) */
+    int32_t v;         /* overlap on each side */
+    int32_t radix;     /* 2 or 4 */
+    int32_t lanes;     /* threads per pair of frames: 1, 2, 4 */
+    int32_t threads;   /* threads per block */
+    int32_t reserved[3];
+} vd_tune;
+
+/*
+ * Creates a code object.  Sec. II-A: constraint length K (3..9), beta
+ * generator polynomials (2..4) each < 2^K with bit K-1 set (they tap the
+ * current input; the corollary of Thm. 2 needs bit 0 set too, which holds for
+ * all standard codes), given as integers whose octal spelling is the
+ * paper's, e.g. 0171.  rate_num/rate_den: the nominal rate after puncturing
+ * (1/beta when unpunctured); checked against the pattern.  puncture: NULL,
+ * or a beta x period row-major 0/1 matrix (period 1..8, no all-zero column)
+ * whose column t mod period says which outputs of stage t are transmitted.
+ * On success *out owns a new object; on failure *out is NULL.
+ * VD_EUNSUPPORTED: a code this build has no kernel for (see vd_code_supported).
+ */
+vd_status vd_code_create(vd_code **out, int K, int beta, const uint32_t *gens_octal,
+                         int rate_num, int rate_den, const uint8_t *puncture, int period);
+
+/* Frees a code object (NULL is ignored). */
+void vd_code_destroy(vd_code *code);
+
+/* 1 if this build has a decode kernel for (K, beta, generators), else 0. */
+int vd_code_supported(int K, int beta, const uint32_t *gens_octal);
+
+/*
+ * Segmented (or full-length) stream decode, Algorithms 1-2 over the frames
+ * of Sec. III.
+ *   d_llr:    device pointer to the received LLRs of the whole stream, of
+ *             llr_type, in transmitted order (kept positions only when the
+ *             code is punctured): n_kept(T) values, T = n_info (+K-1 if
+ *             VD_TERMINATED).  Any alignment.
+ *   n_info:   information bits to decode (0 is a no-op).
+ *   f, v:     frame length and overlap; f must be a multiple of 32 unless
+ *             f >= n_info (a single frame).  v >= 0.  A full-length decode is
+ *             f >= n_info with v >= K-1.
+ *   radix:    2 or 4 (same bits either way).
+ *   flags:    VD_TERMINATED, VD_START_UNKNOWN.
+ *   d_out:    device pointer to ceil(n_info/32) uint32 words (written).
+ *   d_pm:     NULL, or device pointer to n_frames x 2^(K-1) int32 receiving
+ *             each frame's final metrics minus their minimum (for parity
+ *             checks); n_frames = ceil(n_info/f).
+ *   tune:     NULL for the library's choice, else lanes/threads to use
+ *             (f, v and radix come from the arguments).
+ *   stream:   a cudaStream_t (NULL = the legacy default stream).
+ * Errors: VD_EINVAL for bad arguments, VD_EUNSUPPORTED for an LLR type the
+ * code has no kernel for, VD_ENOMEM if scratch cannot grow, VD_ECUDA if a
+ * launch fails.
+ */
+vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_t n_info,
+                    int f, int v, int radix, uint32_t flags, uint32_t *d_out, int32_t *d_pm,
+                    const vd_tune *tune, void *stream);
+
+/* Number of frames of a stream decode: ceil(n_info / f) (0 if n_info <= 0). */
+int64_t vd_num_frames(int64_t n_info, int f);
+
+/* Number of transmitted LLRs for T stages of this code (puncturing applied). */
+int64_t vd_num_kept(const vd_code *code, int64_t T);
+
+/* Bytes of survivor scratch one stream decode needs (informational). */
+int64_t vd_scratch_bytes(const vd_code *code, int64_t n_info, int f, int v, int radix,
+                         const vd_tune *tune);
+
+/* Frees this thread's current device's scratch pool (all streams). */
+vd_status vd_release_scratch(void);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *vd_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int vd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VD_H */

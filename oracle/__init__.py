@@ -86,6 +86,9 @@ def _load():
         lib.or_trace_full_i64.argtypes = [P(_Code), P(i32), i64, ctypes.c_int, ctypes.c_int,
                                           i64, i64, i64, P(u8), P(u32), P(i64), P(i64)]
         lib.or_trace_full_i64.restype = i64
+        lib.or_decode_frames_i64.argtypes = [P(_Code), P(i32), i64, ctypes.c_int, ctypes.c_int,
+                                             i64, i64, P(i64), i64, P(u8), P(i64)]
+        lib.or_decode_frames_i64.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -212,6 +215,27 @@ def decode_f64(code: Code, llr, n_info: int, f: int, v: int, terminated=False,
     if rc != 0:
         raise RuntimeError(f"oracle decode_f64 failed ({rc})")
     return out[: (n_info + 31) // 32], gap[:nwin], mx[:nwin]
+
+
+def decode_frames(code: Code, llr, n_info: int, f: int, v: int, frames, terminated=False,
+                  start_unknown=False, want_pm=False):
+    """Decodes only the listed frames.  Returns bits [n_sel, f] (uint8; only
+    the first e-o of each row are meaningful) and optionally final metrics."""
+    lib = _load()
+    T = n_stages(code, n_info, terminated)
+    llr = np.ascontiguousarray(llr, dtype=np.int32).reshape(-1)
+    if llr.size != T * code.beta:
+        raise ValueError("llr size mismatch")
+    fr = np.ascontiguousarray(frames, dtype=np.int64)
+    bits = np.zeros((fr.size, f), dtype=np.uint8)
+    pm = np.zeros((fr.size, code.n_states), dtype=np.int64) if want_pm else None
+    rc = lib.or_decode_frames_i64(ctypes.byref(code._c), _ptr(llr, ctypes.c_int32), n_info,
+                                  int(bool(terminated)), int(bool(start_unknown)), f, v,
+                                  _ptr(fr, ctypes.c_int64), fr.size, _ptr(bits, ctypes.c_uint8),
+                                  _ptr(pm, ctypes.c_int64) if want_pm else None)
+    if rc != 0:
+        raise RuntimeError(f"oracle decode_frames failed ({rc})")
+    return (bits, pm) if want_pm else bits
 
 
 def encode(code: Code, bits):

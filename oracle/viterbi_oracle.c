@@ -508,3 +508,44 @@ int64_t or_trace_full_i64(const or_code *c, const int32_t *llr, int64_t n_info,
     free(pm); free(pm_new); free(pm0); free(phi);
     return W;
 }
+
+/* ------------------------------------------------ selected frames, int64 */
+
+/*
+ * Decodes only the listed frames of a stream (same rules and arithmetic as
+ * or_decode_i64).  bits_out: [n_sel][f] bytes, frame k's decided bits of
+ * stages [o, e) at bits_out[k*f ..]; final_pm: optional [n_sel][NS].
+ */
+int or_decode_frames_i64(const or_code *c, const int32_t *llr, int64_t n_info,
+                         int terminated, int start_unknown, int64_t f, int64_t v,
+                         const int64_t *frames, int64_t n_sel, uint8_t *bits_out,
+                         int64_t *final_pm)
+{
+    if (or_check_code(c) || n_info <= 0 || f <= 0 || v < 0) return -1;
+    const int NS = 1 << (c->K - 1);
+    int64_t T = n_info + (terminated ? c->K - 1 : 0);
+    int64_t nwin = or_num_windows(n_info, f);
+    int64_t Wmax = f + 2 * v;
+    if (Wmax > T) Wmax = T;
+    uint8_t *bits = (uint8_t *)calloc((size_t)n_info, 1);
+    int64_t *pm = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS);
+    int64_t *pm_new = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS);
+    int64_t *fpm = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS * (size_t)nwin);
+    uint8_t *phi = (uint8_t *)malloc((size_t)Wmax * (size_t)NS);
+    int rc = 0;
+    if (!bits || !pm || !pm_new || !fpm || !phi) { rc = -2; goto done; }
+    for (int64_t k = 0; k < n_sel; ++k) {
+        int64_t s = frames[k];
+        if (s < 0 || s >= nwin) { rc = -1; goto done; }
+        or_job_i64 J = { c, llr, n_info, T, f, v, terminated, start_unknown, bits,
+                         fpm, nwin, 1, 0, 0 };
+        or_window_i64(&J, s, pm, pm_new, phi);
+        or_window w = or_window_of(s, n_info, T, f, v);
+        for (int64_t t = w.o; t < w.e; ++t) bits_out[k * f + (t - w.o)] = bits[t];
+        if (final_pm)
+            for (int j = 0; j < NS; ++j) final_pm[k * NS + j] = fpm[s * NS + j];
+    }
+done:
+    free(bits); free(pm); free(pm_new); free(fpm); free(phi);
+    return rc;
+}

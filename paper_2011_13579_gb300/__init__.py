@@ -1,0 +1,221 @@
+"""Python binding of libvd, the GB300 soft-decision Viterbi decoder.
+
+Thin ctypes layer over the C ABI declared in ``include/vd.h``: the functions
+here carry the same names and only marshal arguments (torch tensors -> device
+pointers, the current CUDA stream -> cudaStream_t).  Every step of decoding
+runs in the library's CUDA kernels; there is no Python or CPU fallback, and
+importing a function whose library is missing raises.
+
+Method: arXiv 2011.13579 (parallel Viterbi decoding over overlapped frames,
+radix-2 and radix-4 add-compare-select).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = [
+    "VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_EUNSUPPORTED", "VD_ETIMEOUT", "VD_EBOUNDS",
+    "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_TERMINATED", "VD_START_UNKNOWN",
+    "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
+    "vd_decode", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_last_error", "vd_version", "Code", "decode",
+]
+
+VD_OK, VD_EINVAL, VD_ENOMEM, VD_ECUDA, VD_EUNSUPPORTED, VD_ETIMEOUT, VD_EBOUNDS = 0, -1, -2, -3, -4, -5, -6
+VD_LLR_S8, VD_LLR_S4, VD_LLR_F16 = 0, 1, 2
+VD_TERMINATED, VD_START_UNKNOWN = 1, 2
+
+_STATUS = {0: "VD_OK", -1: "VD_EINVAL", -2: "VD_ENOMEM", -3: "VD_ECUDA", -4: "VD_EUNSUPPORTED",
+           -5: "VD_ETIMEOUT", -6: "VD_EBOUNDS"}
+
+
+class VdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class VdTune(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_int32), ("v", ctypes.c_int32), ("radix", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles libvd.so for sm_103a (nvcc) in-tree."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded libvd.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libvd.so is not built ({_build.LIB}); call build() first")
+        L = ctypes.CDLL(_build.LIB)
+        P = ctypes.POINTER
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+        L.vd_code_create.argtypes = [P(vp), i32, i32, P(u32), i32, i32, P(ctypes.c_uint8), i32]
+        L.vd_code_create.restype = i32
+        L.vd_code_destroy.argtypes = [vp]
+        L.vd_code_destroy.restype = None
+        L.vd_code_supported.argtypes = [i32, i32, P(u32)]
+        L.vd_code_supported.restype = i32
+        L.vd_decode.argtypes = [vp, vp, i32, i64, i32, i32, i32, u32, vp, vp, P(VdTune), vp]
+        L.vd_decode.restype = i32
+        L.vd_num_frames.argtypes = [i64, i32]
+        L.vd_num_frames.restype = i64
+        L.vd_num_kept.argtypes = [vp, i64]
+        L.vd_num_kept.restype = i64
+        L.vd_scratch_bytes.argtypes = [vp, i64, i32, i32, i32, P(VdTune)]
+        L.vd_scratch_bytes.restype = i64
+        L.vd_release_scratch.argtypes = []
+        L.vd_release_scratch.restype = i32
+        L.vd_last_error.argtypes = []
+        L.vd_last_error.restype = ctypes.c_char_p
+        L.vd_version.argtypes = []
+        L.vd_version.restype = i32
+        _lib = L
+        return L
+
+
+def _check(status):
+    if status != VD_OK:
+        raise VdError(status, vd_last_error())
+    return status
+
+
+def _u32_array(vals):
+    arr = (ctypes.c_uint32 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def vd_last_error() -> str:
+    return (lib().vd_last_error() or b"").decode()
+
+
+def vd_version() -> int:
+    return lib().vd_version()
+
+
+def vd_code_supported(K, gens) -> bool:
+    return bool(lib().vd_code_supported(int(K), len(gens), _u32_array(gens)))
+
+
+def vd_code_create(K, gens, rate=None, puncture=None):
+    """Returns an opaque handle (int) to a new code object; raises VdError."""
+    beta = len(gens)
+    if puncture is not None:
+        rows = [list(map(int, r)) for r in puncture]
+        period = len(rows[0])
+        flat = [x for r in rows for x in r]
+        pbuf = (ctypes.c_uint8 * len(flat))(*flat)
+        kept = sum(flat)
+        rn, rd = rate if rate is not None else (period, kept)
+    else:
+        pbuf, period = None, 1
+        rn, rd = rate if rate is not None else (1, beta)
+    h = ctypes.c_void_p()
+    _check(lib().vd_code_create(ctypes.byref(h), int(K), beta, _u32_array(gens), int(rn), int(rd),
+                                pbuf, int(period)))
+    return h.value
+
+
+def vd_code_destroy(handle) -> None:
+    if handle:
+        lib().vd_code_destroy(ctypes.c_void_p(handle))
+
+
+def vd_num_frames(n_info, f) -> int:
+    return int(lib().vd_num_frames(int(n_info), int(f)))
+
+
+def vd_num_kept(handle, T) -> int:
+    return int(lib().vd_num_kept(ctypes.c_void_p(handle), int(T)))
+
+
+def vd_scratch_bytes(handle, n_info, f, v, radix=2, tune=None) -> int:
+    return int(lib().vd_scratch_bytes(ctypes.c_void_p(handle), int(n_info), int(f), int(v), int(radix),
+                                      ctypes.byref(tune) if tune is not None else None))
+
+
+def vd_release_scratch() -> None:
+    _check(lib().vd_release_scratch())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def vd_decode(handle, llr, llr_type, n_info, f, v, radix, flags, out, pm=None, tune=None, stream=None):
+    """Calls vd_decode on device tensors ``llr`` (received values) and ``out``
+    (ceil(n_info/32) int32/uint32 words), optional ``pm`` (int32 frames x 2^(K-1))."""
+    for name, t in (("llr", llr), ("out", out), ("pm", pm)):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t is not None and not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    _check(lib().vd_decode(ctypes.c_void_p(handle), ctypes.c_void_p(llr.data_ptr()), int(llr_type),
+                           int(n_info), int(f), int(v), int(radix), int(flags),
+                           ctypes.c_void_p(out.data_ptr()),
+                           ctypes.c_void_p(pm.data_ptr()) if pm is not None else None,
+                           ctypes.byref(tune) if tune is not None else None,
+                           _stream_handle(stream)))
+
+
+class Code:
+    """Owning wrapper of a vd_code handle."""
+
+    def __init__(self, K, gens, rate=None, puncture=None):
+        self.K = int(K)
+        self.gens = tuple(int(g) for g in gens)
+        self.beta = len(self.gens)
+        self.puncture = puncture
+        self.handle = vd_code_create(K, gens, rate=rate, puncture=puncture)
+
+    @property
+    def n_states(self):
+        return 1 << (self.K - 1)
+
+    def n_kept(self, T):
+        return vd_num_kept(self.handle, T)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            vd_code_destroy(h)
+
+
+def decode(code: Code, llr, n_info, f, v, radix=2, terminated=False, start_unknown=False,
+           llr_type=VD_LLR_S8, want_pm=False, lanes=0, stream=None, out=None):
+    """Allocates the output words (torch, on llr's device) and decodes."""
+    import torch
+    nw = (int(n_info) + 31) // 32
+    if out is None:
+        out = torch.empty(max(nw, 1), dtype=torch.int32, device=llr.device)
+    pm = None
+    if want_pm:
+        pm = torch.empty((max(vd_num_frames(n_info, f), 1), code.n_states), dtype=torch.int32,
+                         device=llr.device)
+    flags = (VD_TERMINATED if terminated else 0) | (VD_START_UNKNOWN if start_unknown else 0)
+    tune = None
+    if lanes:
+        tune = VdTune()
+        tune.lanes = int(lanes)
+    vd_decode(code.handle, llr, llr_type, n_info, f, v, radix, flags, out, pm, tune, stream)
+    return (out[:nw], pm) if want_pm else out[:nw]

@@ -1,0 +1,48 @@
+// Kernel instantiations for the K=7 code.
+#include "vd_launch.h"
+
+namespace vd {
+
+template <int L, bool R4>
+static cudaError_t launch_one(const StreamParams &p, int64_t blocks, cudaStream_t st) {
+    stream_kernel<7, 2, GENS_K7, L, R4, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_k7(int lanes, bool radix4, const StreamParams &p, int64_t blocks,
+                             cudaStream_t st) {
+    if (radix4) {
+        switch (lanes) {
+        case 1: return launch_one<1, true>(p, blocks, st);
+        case 2: return launch_one<2, true>(p, blocks, st);
+        case 4: return launch_one<4, true>(p, blocks, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (lanes) {
+    case 1: return launch_one<1, false>(p, blocks, st);
+    case 2: return launch_one<2, false>(p, blocks, st);
+    case 4: return launch_one<4, false>(p, blocks, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool geom_k7(int lanes, bool radix4, KernelGeom *g) {
+    switch (lanes) {
+    case 1:
+        g->U = radix4 ? StreamCfg<7, 2, GENS_K7, 1, true>::U : StreamCfg<7, 2, GENS_K7, 1, false>::U;
+        g->NW = radix4 ? StreamCfg<7, 2, GENS_K7, 1, true>::NW : StreamCfg<7, 2, GENS_K7, 1, false>::NW;
+        return true;
+    case 2:
+        g->U = radix4 ? StreamCfg<7, 2, GENS_K7, 2, true>::U : StreamCfg<7, 2, GENS_K7, 2, false>::U;
+        g->NW = radix4 ? StreamCfg<7, 2, GENS_K7, 2, true>::NW : StreamCfg<7, 2, GENS_K7, 2, false>::NW;
+        return true;
+    case 4:
+        g->U = radix4 ? StreamCfg<7, 2, GENS_K7, 4, true>::U : StreamCfg<7, 2, GENS_K7, 4, false>::U;
+        g->NW = radix4 ? StreamCfg<7, 2, GENS_K7, 4, true>::NW : StreamCfg<7, 2, GENS_K7, 4, false>::NW;
+        return true;
+    default: return false;
+    }
+}
+
+}  // namespace vd

@@ -1,0 +1,42 @@
+// Kernel instantiations for the K=9 code.
+#include "vd_launch.h"
+
+namespace vd {
+
+template <int L, bool R4>
+static cudaError_t launch_one(const StreamParams &p, int64_t blocks, cudaStream_t st) {
+    stream_kernel<9, 3, GENS_K9, L, R4, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_k9(int lanes, bool radix4, const StreamParams &p, int64_t blocks,
+                             cudaStream_t st) {
+    if (radix4) {
+        switch (lanes) {
+        case 4: return launch_one<4, true>(p, blocks, st);
+        case 8: return launch_one<8, true>(p, blocks, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (lanes) {
+    case 4: return launch_one<4, false>(p, blocks, st);
+    case 8: return launch_one<8, false>(p, blocks, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool geom_k9(int lanes, bool radix4, KernelGeom *g) {
+    switch (lanes) {
+    case 4:
+        g->U = radix4 ? StreamCfg<9, 3, GENS_K9, 4, true>::U : StreamCfg<9, 3, GENS_K9, 4, false>::U;
+        g->NW = radix4 ? StreamCfg<9, 3, GENS_K9, 4, true>::NW : StreamCfg<9, 3, GENS_K9, 4, false>::NW;
+        return true;
+    case 8:
+        g->U = radix4 ? StreamCfg<9, 3, GENS_K9, 8, true>::U : StreamCfg<9, 3, GENS_K9, 8, false>::U;
+        g->NW = radix4 ? StreamCfg<9, 3, GENS_K9, 8, true>::NW : StreamCfg<9, 3, GENS_K9, 8, false>::NW;
+        return true;
+    default: return false;
+    }
+}
+
+}  // namespace vd

@@ -1,0 +1,391 @@
+// C ABI of the decoder: code objects, argument checks, scratch management and
+// kernel dispatch.  See include/vd.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <utility>
+
+#include "../../include/vd.h"
+#include "vd_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+vd_status fail(vd_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+vd_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(VD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ codes
+
+struct vd_code {
+    int K, beta;
+    uint32_t gens[4];
+    int period;
+    uint8_t punct[4][8];
+    int kept_per_period;
+    int kept_prefix[9];      // kept values before phase p within a period
+    bool punctured;
+    vd::CodeKind kind;
+};
+
+namespace {
+
+vd::CodeKind code_kind(int K, int beta, const uint32_t *g) {
+    if (K == 7 && beta == 2 && g[0] == 0171 && g[1] == 0133) return vd::KIND_K7_R2;
+    if (K == 9 && beta == 3 && g[0] == 0557 && g[1] == 0663 && g[2] == 0711) return vd::KIND_K9_R3;
+    return vd::KIND_NONE;
+}
+
+vd_status check_gens(int K, int beta, const uint32_t *g) {
+    if (K < 3 || K > 9) return fail(VD_EINVAL, "K=%d outside [3, 9]", K);
+    if (beta < 2 || beta > 4) return fail(VD_EINVAL, "beta=%d outside [2, 4]", beta);
+    if (!g) return fail(VD_EINVAL, "generator array is NULL");
+    for (int b = 0; b < beta; ++b) {
+        if (g[b] >= (1u << K)) return fail(VD_EINVAL, "generator %d (0%o) has more than K=%d bits", b, g[b], K);
+        if (!(g[b] >> (K - 1) & 1u))
+            return fail(VD_EINVAL, "generator %d (0%o) does not tap the current input (bit K-1)", b, g[b]);
+    }
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" int vd_code_supported(int K, int beta, const uint32_t *gens_octal) {
+    if (!gens_octal || beta < 2 || beta > 4) return 0;
+    return code_kind(K, beta, gens_octal) != vd::KIND_NONE;
+}
+
+extern "C" vd_status vd_code_create(vd_code **out, int K, int beta, const uint32_t *gens_octal,
+                                    int rate_num, int rate_den, const uint8_t *puncture, int period) {
+    if (!out) return fail(VD_EINVAL, "out is NULL");
+    *out = nullptr;
+    vd_status st = check_gens(K, beta, gens_octal);
+    if (st != VD_OK) return st;
+    vd_code c;
+    memset(&c, 0, sizeof c);
+    c.K = K;
+    c.beta = beta;
+    for (int b = 0; b < beta; ++b) c.gens[b] = gens_octal[b];
+    if (puncture) {
+        if (period < 1 || period > 8) return fail(VD_EINVAL, "puncture period %d outside [1, 8]", period);
+        for (int ph = 0; ph < period; ++ph) {
+            int col = 0;
+            for (int b = 0; b < beta; ++b) {
+                const uint8_t x = puncture[b * period + ph];
+                if (x > 1) return fail(VD_EINVAL, "puncture entry (%d,%d) is not 0/1", b, ph);
+                c.punct[b][ph] = x;
+                col += x;
+            }
+            if (!col) return fail(VD_EINVAL, "puncture column %d transmits nothing", ph);
+        }
+        c.period = period;
+    } else {
+        c.period = 1;
+        for (int b = 0; b < beta; ++b) c.punct[b][0] = 1;
+    }
+    c.kept_prefix[0] = 0;
+    for (int ph = 0; ph < c.period; ++ph) {
+        int col = 0;
+        for (int b = 0; b < beta; ++b) col += c.punct[b][ph];
+        c.kept_prefix[ph + 1] = c.kept_prefix[ph] + col;
+    }
+    c.kept_per_period = c.kept_prefix[c.period];
+    c.punctured = c.kept_per_period != beta * c.period;
+    // nominal rate = period / kept
+    if (rate_num <= 0 || rate_den <= 0 ||
+        (int64_t)rate_num * c.kept_per_period != (int64_t)rate_den * c.period)
+        return fail(VD_EINVAL, "rate %d/%d does not match the pattern (%d/%d)", rate_num, rate_den,
+                    c.period, c.kept_per_period);
+    c.kind = code_kind(K, beta, c.gens);
+    if (c.kind == vd::KIND_NONE)
+        return fail(VD_EUNSUPPORTED, "no decode kernel for K=%d beta=%d with these generators", K, beta);
+    vd_code *p = new (std::nothrow) vd_code(c);
+    if (!p) return fail(VD_ENOMEM, "out of host memory");
+    *out = p;
+    return VD_OK;
+}
+
+extern "C" void vd_code_destroy(vd_code *code) { delete code; }
+
+extern "C" int64_t vd_num_frames(int64_t n_info, int f) {
+    if (n_info <= 0 || f <= 0) return 0;
+    return (n_info + f - 1) / f;
+}
+
+extern "C" int64_t vd_num_kept(const vd_code *c, int64_t T) {
+    if (!c || T < 0) return -1;
+    return (T / c->period) * c->kept_per_period + c->kept_prefix[T % c->period];
+}
+
+// ---------------------------------------------------------------- scratch
+
+namespace {
+
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+std::mutex g_scratch_mu;
+// (device, stream, slot) -> buffer; slot 0 = survivors, 1 = depunctured LLRs
+std::map<std::tuple<int, uintptr_t, int>, Scratch> g_scratch;
+
+vd_status get_scratch(int slot, size_t bytes, cudaStream_t st, void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    Scratch &s = g_scratch[std::make_tuple(dev, (uintptr_t)st, slot)];
+    if (s.bytes < bytes) {
+        if (s.ptr) {
+            // earlier launches on this stream may still read the old buffer
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(s.ptr);
+            s.ptr = nullptr;
+            s.bytes = 0;
+        }
+        size_t want = bytes + bytes / 8;   // headroom against small growth steps
+        e = cudaMalloc(&s.ptr, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s.ptr = nullptr;
+            return fail(VD_ENOMEM, "cannot allocate %zu bytes of scratch: %s", want, cudaGetErrorString(e));
+        }
+        s.bytes = want;
+    }
+    *out = s.ptr;
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_release_scratch(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+        if (std::get<0>(it->first) == dev) {
+            cudaFree(it->second.ptr);
+            it = g_scratch.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return VD_OK;
+}
+
+// ------------------------------------------------------- input pre-pass
+
+namespace {
+
+struct PrepParams {
+    const uint8_t *src;       // kept values: int8, or 4-bit packed (two per byte)
+    int64_t n_kept;           // number of kept values available
+    int64_t T;                // stages to produce
+    int beta, period, kept_per_period, llr_type;
+    uint8_t punct[4][8];
+    int kept_prefix[9];
+    int8_t *dst;              // [T][beta]
+};
+
+__device__ __forceinline__ int8_t kept_value(const PrepParams &p, int64_t k) {
+    if (k >= p.n_kept) return 0;
+    if (p.llr_type == VD_LLR_S4) {
+        const uint8_t byte = p.src[k >> 1];
+        const uint8_t nib = (k & 1) ? (byte >> 4) : (byte & 0x0F);
+        return (int8_t)((int8_t)(nib << 4) >> 4);
+    }
+    return (int8_t)p.src[k];
+}
+
+// Expands the transmitted values of each stage to beta int8 LLRs, with 0 at
+// erased positions (depuncturing) and 4-bit values sign-extended.
+__global__ void prep_kernel(const PrepParams p) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.T) return;
+    const int ph = (int)(t % p.period);
+    int64_t k = (t / p.period) * p.kept_per_period + p.kept_prefix[ph];
+    for (int b = 0; b < p.beta; ++b) {
+        int8_t x = 0;
+        if (p.punct[b][ph]) x = kept_value(p, k++);
+        p.dst[t * p.beta + b] = x;
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- decode
+
+namespace {
+
+bool default_lanes(vd::CodeKind kind, int *lanes) {
+    switch (kind) {
+    case vd::KIND_K7_R2: *lanes = 1; return true;
+    case vd::KIND_K9_R3: *lanes = 4; return true;
+    default: return false;
+    }
+}
+
+bool geometry(vd::CodeKind kind, int lanes, bool r4, vd::KernelGeom *g) {
+    switch (kind) {
+    case vd::KIND_K7_R2: return vd::geom_k7(lanes, r4, g);
+    case vd::KIND_K9_R3: return vd::geom_k9(lanes, r4, g);
+    default: return false;
+    }
+}
+
+struct Plan {
+    int lanes;
+    bool r4;
+    vd::KernelGeom geom;
+    int64_t T, n_win, n_pairs, blocks;
+    int32_t wpad_max;
+    size_t surv_bytes;
+};
+
+vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, uint32_t flags,
+                    const vd_tune *tune, Plan *pl) {
+    pl->r4 = radix == 4;
+    if (tune && tune->lanes > 0) {
+        pl->lanes = tune->lanes;
+    } else if (!default_lanes(c->kind, &pl->lanes)) {
+        return fail(VD_EUNSUPPORTED, "no kernel for this code");
+    }
+    if (!geometry(c->kind, pl->lanes, pl->r4, &pl->geom))
+        return fail(VD_EUNSUPPORTED, "no kernel with %d lanes per frame pair (radix %d) for K=%d",
+                    pl->lanes, radix, c->K);
+    pl->T = n_info + ((flags & VD_TERMINATED) ? c->K - 1 : 0);
+    pl->n_win = vd_num_frames(n_info, f);
+    pl->n_pairs = (pl->n_win + 1) / 2;
+    const int64_t wmax = std::min<int64_t>(pl->T, (int64_t)f + 2 * (int64_t)v);
+    const int64_t wpad = ((wmax + pl->geom.U - 1) / pl->geom.U) * pl->geom.U;
+    if (wpad > (1 << 30)) return fail(VD_EINVAL, "frame too long (%lld stages)", (long long)wmax);
+    pl->wpad_max = (int32_t)wpad;
+    const int64_t threads = pl->n_pairs * pl->lanes;
+    pl->blocks = (threads + vd::kThreads - 1) / vd::kThreads;
+    pl->surv_bytes = (size_t)pl->blocks * vd::kThreads * (size_t)wpad * pl->geom.NW * 4u;
+    return VD_OK;
+}
+
+vd_status check_decode_args(const vd_code *c, const void *d_llr, int llr_type, int64_t n_info, int f,
+                            int v, int radix, uint32_t flags, const uint32_t *d_out) {
+    if (!c) return fail(VD_EINVAL, "code is NULL");
+    if (n_info < 0) return fail(VD_EINVAL, "n_info < 0");
+    if (f <= 0) return fail(VD_EINVAL, "f must be positive");
+    if (v < 0) return fail(VD_EINVAL, "v must be >= 0");
+    if (radix != 2 && radix != 4) return fail(VD_EINVAL, "radix must be 2 or 4");
+    if (flags & ~(uint32_t)(VD_TERMINATED | VD_START_UNKNOWN))
+        return fail(VD_EINVAL, "unknown flag bits 0x%x", flags);
+    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16)
+        return fail(VD_EINVAL, "unknown llr_type %d", llr_type);
+    if (n_info > 0 && (!d_llr || !d_out)) return fail(VD_EINVAL, "NULL device pointer");
+    if (n_info > 0 && f < n_info && f % 32 != 0)
+        return fail(VD_EINVAL, "f=%d must be a multiple of 32 when the stream has several frames", f);
+    if (n_info > ((int64_t)1 << 40)) return fail(VD_EINVAL, "n_info too large");
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t vd_scratch_bytes(const vd_code *c, int64_t n_info, int f, int v, int radix,
+                                    const vd_tune *tune) {
+    if (!c || n_info <= 0 || f <= 0 || v < 0) return 0;
+    Plan pl;
+    if (make_plan(c, n_info, f, v, radix, 0, tune, &pl) != VD_OK) return -1;
+    int64_t extra = 0;
+    if (c->punctured) extra = pl.T * c->beta;
+    return (int64_t)pl.surv_bytes + extra;
+}
+
+extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type, int64_t n_info,
+                               int f, int v, int radix, uint32_t flags, uint32_t *d_out, int32_t *d_pm,
+                               const vd_tune *tune, void *stream) {
+    vd_status st = check_decode_args(c, d_llr, llr_type, n_info, f, v, radix, flags, d_out);
+    if (st != VD_OK) return st;
+    if (n_info == 0) return VD_OK;
+    if (llr_type == VD_LLR_F16) return fail(VD_EUNSUPPORTED, "fp16 LLRs are not built yet");
+    cudaStream_t cs = (cudaStream_t)stream;
+    Plan pl;
+    st = make_plan(c, n_info, f, v, radix, flags, tune, &pl);
+    if (st != VD_OK) return st;
+
+    const int8_t *llr = (const int8_t *)d_llr;
+    if (c->punctured || llr_type == VD_LLR_S4) {
+        void *buf = nullptr;
+        st = get_scratch(1, (size_t)pl.T * c->beta, cs, &buf);
+        if (st != VD_OK) return st;
+        PrepParams pp;
+        memset(&pp, 0, sizeof pp);
+        pp.src = (const uint8_t *)d_llr;
+        pp.n_kept = vd_num_kept(c, pl.T);
+        pp.T = pl.T;
+        pp.beta = c->beta;
+        pp.period = c->period;
+        pp.kept_per_period = c->kept_per_period;
+        pp.llr_type = llr_type;
+        memcpy(pp.punct, c->punct, sizeof pp.punct);
+        memcpy(pp.kept_prefix, c->kept_prefix, sizeof pp.kept_prefix);
+        pp.dst = (int8_t *)buf;
+        const int tb = 256;
+        prep_kernel<<<(unsigned)((pl.T + tb - 1) / tb), tb, 0, cs>>>(pp);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "input pre-pass launch");
+        llr = (const int8_t *)buf;
+    }
+
+    void *surv = nullptr;
+    st = get_scratch(0, pl.surv_bytes, cs, &surv);
+    if (st != VD_OK) return st;
+
+    vd::StreamParams p;
+    p.llr = llr;
+    p.llr_bytes = pl.T * c->beta;
+    p.n_info = n_info;
+    p.T = pl.T;
+    p.f = f;
+    p.v = v;
+    p.n_win = pl.n_win;
+    p.n_pairs = pl.n_pairs;
+    p.flags = flags;
+    p.wpad_max = pl.wpad_max;
+    p.out = d_out;
+    p.surv = (uint32_t *)surv;
+    p.pm_out = d_pm;
+    if (pl.blocks > 0x7FFFFFFF) return fail(VD_EINVAL, "stream too long for one launch");
+    cudaError_t e;
+    switch (c->kind) {
+    case vd::KIND_K7_R2: e = vd::launch_stream_k7(pl.lanes, pl.r4, p, pl.blocks, cs); break;
+    case vd::KIND_K9_R3: e = vd::launch_stream_k9(pl.lanes, pl.r4, p, pl.blocks, cs); break;
+    default: return fail(VD_EUNSUPPORTED, "no kernel for this code");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    return VD_OK;
+}
+
+extern "C" const char *vd_last_error(void) { return g_err.c_str(); }
+
+extern "C" int vd_version(void) { return 100; }

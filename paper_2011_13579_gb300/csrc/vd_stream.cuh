@@ -1,0 +1,601 @@
+// Segmented stream decode: branch metrics, radix-2 / radix-4 add-compare-select
+// with packed survivors, and traceback from the overlap, fused in one kernel.
+//
+// Paper: arXiv 2011.13579.  Eq. BM (branch metric), Eq. PM / Eq. SP0 (ACS and
+// survivor), Algorithms 1 and 2 (forward and backward procedures), Sec. III
+// (frames of f stages with overlap), Thm. 1 (butterfly state indices),
+// Thm. 2 and its corollary (all four branch outputs of a butterfly follow
+// from its main output), Sec. VIII-A / Eq. radix4:PM, radix4:SP0 (two stages
+// per step, traceback two stages per step).
+//
+// Mapping (one group of L lanes per PAIR of frames):
+//   * the two frames of a pair are the two 16-bit halves of every register;
+//   * register R (K-1 bits; the top log2(L) bits select the lane) holds, at
+//     stage tau, the metric of state ROTR^tau(R).  With this rotation the two
+//     left states 2g, 2g+1 of every butterfly sit in registers that differ
+//     only in bit (tau mod (K-1)), and its two right states g, g+2^(K-2) land
+//     in the same two registers: the ACS is in place.  When that bit is a
+//     lane bit the partner comes from the other lane by one shuffle;
+//   * the main output alpha of butterfly g is linear in the bits of g, so the
+//     part contributed by the lane bits is folded into the LLR signs of that
+//     lane and the rest is a compile-time constant per register;
+//   * frames of a pair are right-aligned on a common padded length Wpad (a
+//     multiple of the unroll period U), so they end together; the shorter
+//     frame is preceded by stages of zero LLRs, which keep all-equal metrics
+//     all-equal, and a frame that starts from the reset state is re-seeded
+//     when its first stage arrives;
+//   * decisions go, packed one bit per state and frame, to a global scratch
+//     buffer; a warp's stores for one stage are contiguous.  Bit (r & 31) of
+//     word (r >> 5) holds register r of the lane (r & 15 at bit 16h for a
+//     lane with 16 registers; frame h = 0, 1);
+//   * radix-4: stages are taken in pairs (t-1, t).  The metrics are two
+//     radix-2 steps (grouping the four candidates of a right state by their
+//     middle state, as Eq. radix4:PM allows, gives exactly the same integers
+//     and ties), and the survivor of right state j is the 2-bit pair
+//     (d_m, d_i): the decision of j at stage t and the decision of the
+//     middle state it selects at stage t-1, stored at the same bit position
+//     so that one traceback step crosses two stages.
+#pragma once
+#include <utility>
+#include "vd_device.cuh"
+
+namespace vd {
+
+struct StreamParams {
+    const int8_t *llr;      // depunctured received LLRs, [T][beta], int8
+    int64_t llr_bytes;      // T * beta
+    int64_t n_info, T, f, v;
+    int64_t n_win, n_pairs;
+    uint32_t flags;         // bit0: terminated, bit1: start state unknown
+    int32_t wpad_max;       // padded frame length used as the scratch stage stride
+    uint32_t *out;          // packed decoded bits, LSB-first
+    uint32_t *surv;         // survivor scratch
+    int32_t *pm_out;        // optional [n_win][2^(K-1)] canonical final metrics
+};
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Unroll period: an even multiple of K-1 (rotation period) whose chunk of LLR
+// bytes is a whole number of 32-bit words.
+__host__ __device__ constexpr int chunk_stages(int K, int beta) {
+    int u = K - 1;
+    while ((u * beta) % 4 || (u % 2)) u += K - 1;
+    return u;
+}
+
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4>
+struct StreamCfg {
+    using C = Code<K, BETA, GENS>;
+    static constexpr int NB = C::NB;
+    static constexpr int NS = C::NS;
+    static constexpr int NR = NS / L;                 // registers per lane
+    static constexpr int LR = ilog2(NR);              // local register bits
+    static constexpr int U = chunk_stages(K, BETA);   // stages per chunk
+    static constexpr int UW = U * BETA / 4;           // LLR words per chunk per frame
+    static constexpr int NW = NR >= 32 ? NR / 16 : 1; // survivor words per lane per stage
+    static constexpr int WPF = NR >= 32 ? NR / 32 : 1;// survivor words per frame per lane per stage
+    static constexpr int NACC = NR >= 16 ? NR / 16 : 1;
+    // normalisation period (multiple of U), see the header of vd_device.cuh
+    static constexpr int NMAX = (32767 - 2 * C::S) / (2 * C::B) - 1;
+    static constexpr int NORM_CHUNKS = (NMAX / U) > 0 ? (NMAX / U) : 1;
+    static constexpr int F = (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
+    static_assert(NS % L == 0 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
+    static_assert(NR >= 2, "at least one butterfly per lane");
+    static_assert(!RADIX4 || NB % 2 == 0, "radix-4 pairs need an even rotation period");
+    static_assert(NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
+    static_assert(F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767, "metric range");
+};
+
+template <typename Fn, int... S>
+__device__ __forceinline__ void static_for_impl(Fn &&fn, std::integer_sequence<int, S...>) {
+    (fn(std::integral_constant<int, S>{}), ...);
+}
+// Calls fn(integral_constant<int, i>) for i = 0 .. N-1: loop indices are compile-time.
+template <int N, typename Fn>
+__device__ __forceinline__ void static_for(Fn &&fn) {
+    static_for_impl(fn, std::make_integer_sequence<int, N>{});
+}
+
+// Loads bytes [vb, vb + 4*UW) of the LLR stream as UW words, zero outside [lo, hi).
+template <int UW>
+__device__ __forceinline__ void load_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
+                                           uint32_t (&w)[UW]) {
+    if (vb >= lo && vb + 4 * UW <= hi) {
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(llr) + (uintptr_t)vb;
+        const uint32_t mis = (uint32_t)(addr & 3u);
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(addr - mis);
+        uint32_t raw[UW + 1];
+#pragma unroll
+        for (int i = 0; i < UW; ++i) raw[i] = __ldg(p + i);
+        // the extra word holds the last bytes of the chunk when it is misaligned;
+        // it contains at least one byte inside the stream, so it is readable
+        raw[UW] = mis ? __ldg(p + UW) : 0u;
+#pragma unroll
+        for (int i = 0; i < UW; ++i) w[i] = funnel_r(raw[i], raw[i + 1], 8u * mis);
+    } else {
+#pragma unroll
+        for (int i = 0; i < UW; ++i) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t pos = vb + 4 * i + k;
+                if (pos >= lo && pos < hi) x |= (uint32_t)(uint8_t)llr[pos] << (8 * k);
+            }
+            w[i] = x;
+        }
+    }
+}
+
+// Selects element idx of a small register array without local memory.
+template <int N>
+__device__ __forceinline__ uint32_t pick(const uint32_t *a, uint32_t idx) {
+    uint32_t r = a[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) r = (idx == (uint32_t)i) ? a[i] : r;
+    return r;
+}
+
+// Mask of bit positions whose bit k is set (k < 5).
+__host__ __device__ constexpr uint32_t bitk_mask(int k) {
+    return k == 0 ? 0xAAAAAAAAu : k == 1 ? 0xCCCCCCCCu : k == 2 ? 0xF0F0F0F0u
+         : k == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+__global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
+    using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
+    using C = typename Cfg::C;
+    constexpr int NB = Cfg::NB, NR = Cfg::NR, LR = Cfg::LR, U = Cfg::U, UW = Cfg::UW;
+    constexpr int NW = Cfg::NW, WPF = Cfg::WPF, NACC = Cfg::NACC;
+    constexpr uint32_t LV = C::lv(), MV = C::mv();
+    constexpr uint32_t F2 = (uint32_t)Cfg::F * 0x00010001u;
+    constexpr uint32_t SEED0 = (uint32_t)(Cfg::F + C::S) * 0x00010001u;  // state 0 after a reset
+    constexpr uint32_t SEEDX = (uint32_t)Cfg::F * 0x00010001u;           // other states after a reset
+
+    const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t q = gtid / L;
+    const int lane = (int)(gtid % L);
+    if (q >= p.n_pairs) return;   // whole lane groups leave together
+    const unsigned warp_lane = threadIdx.x & 31u;
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu
+                                     : (((1u << L) - 1u) << (warp_lane & ~(unsigned)(L - 1)));
+    const int grp_base = (int)(warp_lane & ~(unsigned)(L - 1));
+
+    // ---------------------------------------------------------- frame plan
+    int64_t fa[2], fb[2], fo[2], fe[2];
+    bool known[2], term[2], valid[2];
+    int64_t W[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t s = 2 * q + h;
+        valid[h] = s < p.n_win;
+        Frame w = frame_of(valid[h] ? s : 0, p.n_info, p.T, p.f, p.v, p.flags);
+        fa[h] = w.a; fb[h] = w.b; fo[h] = w.o; fe[h] = w.e;
+        known[h] = valid[h] && w.known_start;
+        term[h] = valid[h] && w.term_end;
+        W[h] = valid[h] ? (w.b - w.a) : 0;
+    }
+    const int64_t Wmax = W[0] > W[1] ? W[0] : W[1];
+    const int Wpad = (int)(((Wmax + U - 1) / U) * U);
+    int tau0[2], tauo[2], taue[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        tau0[h] = Wpad - (int)W[h];
+        tauo[h] = valid[h] ? tau0[h] + (int)(fo[h] - fa[h]) : Wpad;
+        taue[h] = valid[h] ? tau0[h] + (int)(fe[h] - fa[h]) : Wpad;
+    }
+    const int tau_store = tauo[0] < tauo[1] ? tauo[0] : tauo[1];
+    const int reset_at0 = known[0] ? tau0[0] : -1;
+    const int reset_at1 = known[1] ? tau0[1] : -1;
+
+    // lane part of the branch output per phase, folded into LLR signs
+    uint32_t cbits = 0;
+    if constexpr (L > 1) {
+#pragma unroll
+        for (int ph = 0; ph < NB; ++ph) {
+            uint32_t lp = (uint32_t)lane;
+            if (ph >= LR) lp &= ~(1u << (ph - LR));
+            const uint32_t G = C::rotr(lp << LR, ph) >> 1;
+            cbits |= alpha_rt<K, BETA, GENS>(G) << (ph * BETA);
+        }
+    }
+
+    // ------------------------------------------------------------ metrics
+    uint32_t P[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) P[r] = SEED0;   // all-equal: unknown start
+
+    uint32_t *const surv_blk = p.surv + (size_t)blockIdx.x * (size_t)p.wpad_max * NT * NW;
+    const int64_t vb0 = (fa[0] - tau0[0]) * BETA, vb1 = (fa[1] - tau0[1]) * BETA;
+    const int64_t lo0 = fa[0] * BETA, hi0 = valid[0] ? fb[0] * BETA : lo0;
+    const int64_t lo1 = fa[1] * BETA, hi1 = valid[1] ? fb[1] * BETA : lo1;
+
+    auto store_words = [&](int tau, const uint32_t (&wd)[NW]) {
+        uint32_t *dst = surv_blk + ((size_t)tau * NT + threadIdx.x) * NW;
+        if constexpr (NW == 1) {
+            *dst = wd[0];
+        } else if constexpr (NW == 2) {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(wd[0], wd[1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NW; i += 4)
+                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(wd[i], wd[i + 1], wd[i + 2], wd[i + 3]);
+        }
+    };
+
+    const int nchunks = Wpad / U;
+    for (int c = 0; c < nchunks; ++c) {
+        uint32_t cw0[UW], cw1[UW];
+        load_chunk<UW>(p.llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cw0);
+        load_chunk<UW>(p.llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cw1);
+        uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
+
+        static_for<U>([&](auto Sc) {
+            constexpr int S = decltype(Sc)::value;
+            constexpr int PH = S % NB;
+            const int tau = c * U + S;
+
+            // re-seed a frame that starts from the reset state (state 0 is
+            // register 0 at every stage: ROTR of 0 is 0)
+            if (tau == reset_at0 || tau == reset_at1) {
+                const uint32_t hm = (tau == reset_at0 ? 0x0000FFFFu : 0u) |
+                                    (tau == reset_at1 ? 0xFFFF0000u : 0u);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t val = (r == 0 && lane == 0) ? SEED0 : SEEDX;
+                    P[r] = (P[r] & ~hm) | (val & hm);
+                }
+            }
+
+            // ---- branch metrics of this stage (Eq. BM), both frames at once
+            uint32_t Lb[BETA];
+#pragma unroll
+            for (int b = 0; b < BETA; ++b) {
+                const int j = S * BETA + b;
+                const uint32_t k = (uint32_t)(j & 3);
+                const uint32_t sel = k | ((k + 8u) << 4) | ((k + 4u) << 8) | ((k + 12u) << 12);
+                Lb[b] = prmt(cw0[j >> 2], cw1[j >> 2], sel);   // sign-extended int8 pair
+                if constexpr (L > 1) {
+                    const uint32_t m = 0u - ((cbits >> (PH * BETA + b)) & 1u);
+                    Lb[b] = sub_s16x2(Lb[b] ^ m, m);
+                }
+            }
+            // A[x] = sum_b (-1)^{x_b} l_b for every output pattern x
+            uint32_t A[1 << BETA];
+            A[0] = Lb[0];
+            A[1] = sub_s16x2(0u, Lb[0]);
+#pragma unroll
+            for (int b = 1; b < BETA; ++b) {
+#pragma unroll
+                for (int x = 0; x < (1 << b); ++x) {
+                    A[x | (1 << b)] = sub_s16x2(A[x], Lb[b]);
+                    A[x] = add_s16x2(A[x], Lb[b]);
+                }
+            }
+
+            // ---- add-compare-select (Eq. PM), decisions (Eq. SP0), packing
+            uint32_t X[NR];
+            uint32_t acc[NACC];
+#pragma unroll
+            for (int i = 0; i < NACC; ++i) acc[i] = 0;
+
+            auto butterfly = [&](int ra) {   // local pair (ra, ra | 1 << PH)
+                const int rb = ra | (1 << PH);
+                const uint32_t a = C::alpha(C::rotr((uint32_t)ra, PH) >> 1);
+                const uint32_t Pa = P[ra], Pb = P[rb];
+                // even -> j0: alpha, odd -> j0: alpha^LV, even -> j1: alpha^MV, odd -> j1: alpha^MV^LV
+                const uint32_t cb0 = add_u16x2(Pb, A[a ^ LV]);
+                const uint32_t cb1 = add_u16x2(Pb, A[a ^ MV ^ LV]);
+                const uint32_t e0 = add_u16x2(sub_s16x2(A[a ^ LV], A[a]), 0x80008000u);
+                const uint32_t e1 = add_u16x2(sub_s16x2(A[a ^ MV ^ LV], A[a ^ MV]), 0x80008000u);
+                P[ra] = addmax_u16x2(Pa, A[a], cb0);
+                P[rb] = addmax_u16x2(Pa, A[a ^ MV], cb1);
+                X[ra] = Pb - Pa + e0;   // bit 15 / 31 set: odd predecessor wins or ties
+                X[rb] = Pb - Pa + e1;
+            };
+            auto cross = [&](int r) {   // partner register in lane ^ (1 << (PH - LR))
+                constexpr int lb = PH >= LR ? PH - LR : 0;
+                const uint32_t xb = ((uint32_t)lane >> lb) & 1u;   // 1: this lane holds R_b
+                const uint32_t a = C::alpha(C::rotr((uint32_t)r, PH) >> 1);
+                const uint32_t own = P[r];
+                const uint32_t oth = __shfl_xor_sync(gmask, own, 1 << lb);
+                const uint32_t d_own = xb ? A[a ^ MV ^ LV] : A[a];
+                const uint32_t d_oth = xb ? A[a ^ MV] : A[a ^ LV];
+                // holder of R_a: bit = (c_oth >= c_own); holder of R_b: bit = !(c_own >= c_oth),
+                // inverted back after packing
+                const uint32_t e = add_u16x2(sub_s16x2(d_oth, d_own), 0x80008000u) - (xb ? 0x00010001u : 0u);
+                P[r] = addmax_u16x2(own, d_own, add_u16x2(oth, d_oth));
+                X[r] = oth - own + e;
+            };
+            auto pack_block = [&](int blk) {   // 16 registers -> acc[blk]
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int r1 = 16 * blk + kk;
+                    const uint32_t t = prmt(X[r1], X[r1 + 8], 0xFDB9u);
+                    acc[blk] |= t & (0x01010101u << kk);
+                }
+            };
+
+            if constexpr (NR >= 16) {
+                if constexpr (PH < LR) {
+                    // process blocks of 16 registers (block pairs when the
+                    // butterfly partner is in another block) and pack each
+                    // block as soon as it is complete
+#pragma unroll
+                    for (int blk = 0; blk < NR / 16; ++blk) {
+                        if (PH >= 4 && (blk & (1 << (PH - 4)))) continue;
+#pragma unroll
+                        for (int r = 16 * blk; r < 16 * blk + 16; ++r)
+                            if (!(r & (1 << PH))) butterfly(r);
+                        pack_block(blk);
+                        if (PH >= 4) pack_block(blk | (1 << (PH - 4)));
+                    }
+                } else {
+#pragma unroll
+                    for (int blk = 0; blk < NR / 16; ++blk) {
+#pragma unroll
+                        for (int r = 16 * blk; r < 16 * blk + 16; ++r) cross(r);
+                        pack_block(blk);
+                    }
+                }
+            } else {
+                if constexpr (PH < LR) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        if (!(r & (1 << PH))) butterfly(r);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) cross(r);
+                }
+            }
+
+            // ---- regroup into per-frame words, natural bit order
+            uint32_t wd[NW];
+            if constexpr (NR >= 32) {
+#pragma unroll
+                for (int m = 0; m < WPF; ++m) {
+                    wd[m] = prmt(acc[2 * m], acc[2 * m + 1], 0x6420u);
+                    wd[WPF + m] = prmt(acc[2 * m], acc[2 * m + 1], 0x7531u);
+                }
+            } else if constexpr (NR == 16) {
+                wd[0] = prmt(acc[0], acc[0], 0x3120u);
+            } else {
+                uint32_t x = 0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    x |= ((X[r] >> 15) & 1u) << r | ((X[r] >> 31) & 1u) << (16 + r);
+                wd[0] = x;
+            }
+            if constexpr (PH >= LR) {
+                const uint32_t inv = 0u - (((uint32_t)lane >> (PH - LR)) & 1u);
+#pragma unroll
+                for (int i = 0; i < NW; ++i) wd[i] ^= inv;
+            }
+
+            if constexpr (!RADIX4) {
+                if (tau >= tau_store) store_words(tau, wd);
+            } else if constexpr ((S & 1) == 0) {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) W1[i] = wd[i];
+            } else {
+                // second stage of a pair: low[R] = W1[R with bit PH := d_m(R)]
+                uint32_t lo_w[NW];
+                if constexpr (PH < 5 && PH < LR) {
+                    constexpr uint32_t m1 = bitk_mask(PH), m0 = ~m1;
+                    constexpr int sh = 1 << PH;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) {
+                        const uint32_t e0 = (W1[i] & m0) | ((W1[i] & m0) << sh);
+                        const uint32_t e1 = (W1[i] & m1) | ((W1[i] & m1) >> sh);
+                        lo_w[i] = (wd[i] & e1) | (~wd[i] & e0);
+                    }
+                } else if constexpr (PH < LR) {
+                    constexpr int wb = 1 << (PH - 5);   // word-index bit (NR >= 64)
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) {
+                        const int base = (i / WPF) * WPF, w = i % WPF;
+                        const uint32_t e0 = W1[base + (w & ~wb)], e1 = W1[base + (w | wb)];
+                        lo_w[i] = (wd[i] & e1) | (~wd[i] & e0);
+                    }
+                } else {
+                    constexpr int lb = PH - LR;
+                    const bool xb = ((lane >> lb) & 1) != 0;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) {
+                        const uint32_t oth = __shfl_xor_sync(gmask, W1[i], 1 << lb);
+                        const uint32_t e0 = xb ? oth : W1[i], e1 = xb ? W1[i] : oth;
+                        lo_w[i] = (wd[i] & e1) | (~wd[i] & e0);
+                    }
+                }
+                if (tau >= tau_store) {
+                    store_words(tau, wd);
+                    store_words(tau - 1, lo_w);
+                }
+            }
+        });
+
+        // ---- normalisation: subtract state 0's metric, add F+S, clamp at F
+        if ((c + 1) % Cfg::NORM_CHUNKS == 0) {
+            uint32_t ref = P[0];
+            if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
+            const uint32_t t = sub_s16x2(SEED0, ref);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
+        }
+    }
+
+    // ------------------------------------------------- traceback start state
+    // After Wpad stages (a multiple of K-1) register R holds state R again.
+    uint32_t R[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t best = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
+            const uint32_t Rg = ((uint32_t)lane << LR) | (uint32_t)r;
+            const uint32_t key = (v << 16) | (0xFFFFu - Rg);
+            best = best > key ? best : key;
+        }
+        if constexpr (L > 1) {
+#pragma unroll
+            for (int m = 1; m < L; m <<= 1) {
+                const uint32_t o = __shfl_xor_sync(gmask, best, m);
+                best = best > o ? best : o;
+            }
+        }
+        R[h] = term[h] ? 0u : (0xFFFFu - (best & 0xFFFFu));
+    }
+
+    // optional canonical final metrics (lambda - min lambda), for parity checks
+    if (p.pm_out) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t mn = 0xFFFFu;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
+                mn = mn < v ? mn : v;
+            }
+            if constexpr (L > 1) {
+#pragma unroll
+                for (int m = 1; m < L; m <<= 1) {
+                    const uint32_t o = __shfl_xor_sync(gmask, mn, m);
+                    mn = mn < o ? mn : o;
+                }
+            }
+            if (valid[h]) {
+                int32_t *dst = p.pm_out + (2 * q + h) * (int64_t)C::NS + ((int64_t)lane << LR);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
+                    dst[r] = (int32_t)v - (int32_t)mn;
+                }
+            }
+        }
+    }
+
+    // -------------------------------------------------------------- traceback
+    // Every lane of the group follows both frames; the lane that owns the
+    // current register supplies the decision bit (one shuffle).  Stages are
+    // walked in groups of K-1 starting at Wpad-1, so the phase of every stage
+    // in a group is a compile-time constant; the next group's survivor words
+    // are loaded while the current group is walked.
+    constexpr int G = NB;
+    uint32_t oacc[2] = {0u, 0u};
+    const int64_t toff0 = fa[0] - tau0[0], toff1 = fa[1] - tau0[1];
+    const uint32_t *my = surv_blk + (size_t)threadIdx.x * NW;
+
+    auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
+        // bit of register Rh of frame h in this lane's words for one stage
+        uint32_t word, bit;
+        if constexpr (NR >= 32) {
+            word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
+            bit = Rh & 31u;
+        } else {
+            word = wd[0];
+            bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
+        }
+        return (word >> bit) & 1u;
+    };
+    auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
+        if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
+        else return bits;
+    };
+    auto emit = [&](int h, int t, uint32_t u) {
+        if (t < taue[h]) {
+            oacc[h] = (oacc[h] << 1) | u;
+            const int64_t tabs = (int64_t)t + (h ? toff1 : toff0);
+            if ((tabs & 31) == 0) {
+                if (lane == (L > 1 ? h : 0)) p.out[tabs >> 5] = oacc[h];
+                oacc[h] = 0;
+            }
+        }
+    };
+
+    uint32_t bufA[G][NW], bufB[G][NW];
+    auto load_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int t = t0 - g;
+            const uint32_t *src = my + (size_t)t * NT * NW;
+            if (t >= tau_store) {
+                if constexpr (NW == 1) {
+                    buf[g][0] = __ldg(src);
+                } else if constexpr (NW == 2) {
+                    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(src));
+                    buf[g][0] = x.x; buf[g][1] = x.y;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NW; i += 4) {
+                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + i));
+                        buf[g][i] = x.x; buf[g][i + 1] = x.y; buf[g][i + 2] = x.z; buf[g][i + 3] = x.w;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) buf[g][i] = 0u;
+            }
+        }
+    };
+    auto walk_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+        if constexpr (!RADIX4) {
+            static_for<G>([&](auto gc) {
+                constexpr int g = decltype(gc)::value;
+                constexpr int ph = NB - 1 - g;     // t0 = -1 mod (K-1)
+                const int t = t0 - g;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (t >= tauo[h]) {
+                        const uint32_t d = owner_bits(decision(buf[g], h, R[h]), R[h]);
+                        const uint32_t u = (R[h] >> ph) & 1u;
+                        R[h] = (R[h] & ~(1u << ph)) | (d << ph);
+                        emit(h, t, u);
+                    }
+                }
+            });
+        } else {
+            // pairs (t, t-1): t is the second stage of a pair (odd offset in a chunk)
+            static_for<G / 2>([&](auto gc) {
+                constexpr int g = 2 * decltype(gc)::value;
+                constexpr int ph2 = NB - 1 - g, ph1 = NB - 2 - g;
+                const int t = t0 - g;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (t >= tauo[h]) {
+                        const uint32_t b2 = decision(buf[g], h, R[h]);
+                        const uint32_t b1 = decision(buf[g + 1], h, R[h]);   // same position
+                        const uint32_t bb = owner_bits(b2 | (b1 << 1), R[h]);
+                        const uint32_t u2 = (R[h] >> ph2) & 1u;
+                        const uint32_t m = (R[h] & ~(1u << ph2)) | ((bb & 1u) << ph2);
+                        emit(h, t, u2);
+                        if (t - 1 >= tauo[h]) {
+                            const uint32_t u1 = (m >> ph1) & 1u;
+                            R[h] = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
+                            emit(h, t - 1, u1);
+                        } else {
+                            R[h] = m;
+                        }
+                    }
+                }
+            });
+        }
+    };
+
+    int t0 = Wpad - 1;
+    if (t0 >= tau_store) {
+        load_group(t0, bufA);
+        while (true) {
+            if (t0 - G >= tau_store) load_group(t0 - G, bufB);
+            walk_group(t0, bufA);
+            t0 -= G;
+            if (t0 < tau_store) break;
+            if (t0 - G >= tau_store) load_group(t0 - G, bufA);
+            walk_group(t0, bufB);
+            t0 -= G;
+            if (t0 < tau_store) break;
+        }
+    }
+}
+
+}  // namespace vd

@@ -499,3 +499,20 @@ def test_depuncture_roundtrip():
         assert np.all(back[~mask] == 0)
         with pytest.raises(ValueError):
             oracle.depuncture(code, kept[:-1], T)
+
+
+def test_decode_frames_matches_full_decode():
+    """The frame-subset entry point returns the same bits and metrics as the
+    whole-stream decode for the frames it is asked for."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    code = K7
+    n, f, v = 3000, 256, 42
+    llr = rng.integers(-127, 128, size=(n, 2)).astype(np.int32)
+    words, pm = oracle.decode(code, llr, n, f=f, v=v, want_pm=True)
+    allbits = oracle.unpack_bits(words, n)
+    frames = [0, 3, 11]
+    bits, pm_sel = oracle.decode_frames(code, llr, n, f, v, frames, want_pm=True)
+    for k, s in enumerate(frames):
+        e = min(n, (s + 1) * f)
+        assert np.array_equal(bits[k, : e - s * f], allbits[s * f: e])
+        assert np.array_equal(pm_sel[k], pm[s])
