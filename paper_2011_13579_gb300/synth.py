@@ -66,7 +66,7 @@ def conv_encode(K: int, gens, bits: np.ndarray) -> np.ndarray:
     for b, g in enumerate(gens):
         taps = np.array([(g >> (K - 1 - d)) & 1 for d in range(K)], dtype=np.int32)
         acc = np.zeros(n, dtype=np.int32)
-        for d in range(K):
+        for d in range(min(K, n)):
             if taps[d]:
                 acc[d:] += bits[: n - d]
         out[:, b] = (acc & 1).astype(np.uint8)
