@@ -135,6 +135,13 @@ vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_
                     int f, int v, int radix, uint32_t flags, uint32_t *d_out, int32_t *d_pm,
                     const vd_tune *tune, void *stream);
 
+/*
+ * Waits for the stream, then reads and clears the library's device status
+ * word.  VD_EBOUNDS if a kernel refused work that would have overrun its
+ * scratch since the last check (the affected outputs are not written).
+ */
+vd_status vd_sync(void *stream);
+
 /* Number of frames of a stream decode: ceil(n_info / f) (0 if n_info <= 0). */
 int64_t vd_num_frames(int64_t n_info, int f);
 

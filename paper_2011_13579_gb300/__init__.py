@@ -21,7 +21,7 @@ __all__ = [
     "VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_EUNSUPPORTED", "VD_ETIMEOUT", "VD_EBOUNDS",
     "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_TERMINATED", "VD_START_UNKNOWN",
     "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
-    "vd_decode", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_decode", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -79,6 +79,8 @@ def lib():
         L.vd_num_kept.restype = i64
         L.vd_scratch_bytes.argtypes = [vp, i64, i32, i32, i32, P(VdTune)]
         L.vd_scratch_bytes.restype = i64
+        L.vd_sync.argtypes = [vp]
+        L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
         L.vd_release_scratch.restype = i32
         L.vd_last_error.argtypes = []
@@ -147,6 +149,11 @@ def vd_num_kept(handle, T) -> int:
 def vd_scratch_bytes(handle, n_info, f, v, radix=2, tune=None) -> int:
     return int(lib().vd_scratch_bytes(ctypes.c_void_p(handle), int(n_info), int(f), int(v), int(radix),
                                       ctypes.byref(tune) if tune is not None else None))
+
+
+def vd_sync(stream=None) -> None:
+    """Waits for the stream and raises VdError if a kernel reported a device-side error."""
+    _check(lib().vd_sync(_stream_handle(stream)))
 
 
 def vd_release_scratch() -> None:

@@ -13,6 +13,7 @@
 #include <utility>
 
 #include "../../include/vd.h"
+#include "vd_code.h"
 #include "vd_launch.h"
 
 namespace {
@@ -37,16 +38,6 @@ vd_status cuda_fail(cudaError_t e, const char *what) {
 
 // ------------------------------------------------------------------ codes
 
-struct vd_code {
-    int K, beta;
-    uint32_t gens[4];
-    int period;
-    uint8_t punct[4][8];
-    int kept_per_period;
-    int kept_prefix[9];      // kept values before phase p within a period
-    bool punctured;
-    vd::CodeKind kind;
-};
 
 namespace {
 
@@ -178,7 +169,54 @@ vd_status get_scratch(int slot, size_t bytes, cudaStream_t st, void **out) {
     return VD_OK;
 }
 
+// Library-owned device status word (per device): kernels OR error bits into it.
+vd_status device_status_word(cudaStream_t st, int **out) {
+    void *p = nullptr;
+    bool fresh = false;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        Scratch &s = g_scratch[std::make_tuple(dev, (uintptr_t)0, 2)];
+        if (!s.ptr) {
+            e = cudaMalloc(&s.ptr, 256);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(VD_ENOMEM, "cannot allocate the device status word");
+            }
+            s.bytes = 256;
+            fresh = true;
+        }
+        p = s.ptr;
+    }
+    if (fresh) {
+        cudaError_t e = cudaMemset(p, 0, 256);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    }
+    (void)st;
+    *out = (int *)p;
+    return VD_OK;
+}
+
 }  // namespace
+
+extern "C" vd_status vd_sync(void *stream) {
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int *status = nullptr;
+    vd_status st = device_status_word(cs, &status);
+    if (st != VD_OK) return st;
+    int h = 0;
+    e = cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    if (h) {
+        cudaMemset(status, 0, sizeof h);
+        return fail(VD_EBOUNDS, "a device-side bounds check fired (status 0x%x)", h);
+    }
+    return VD_OK;
+}
 
 extern "C" vd_status vd_release_scratch(void) {
     int dev = 0;
@@ -375,6 +413,10 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     p.out = d_out;
     p.surv = (uint32_t *)surv;
     p.pm_out = d_pm;
+    int *status = nullptr;
+    st = device_status_word(cs, &status);
+    if (st != VD_OK) return st;
+    p.status = status;
     if (pl.blocks > 0x7FFFFFFF) return fail(VD_EINVAL, "stream too long for one launch");
     cudaError_t e;
     switch (c->kind) {
@@ -387,5 +429,7 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
 }
 
 extern "C" const char *vd_last_error(void) { return g_err.c_str(); }
+
+void vd_internal_set_error(const char *msg) { g_err = msg; }
 
 extern "C" int vd_version(void) { return 100; }

@@ -47,11 +47,39 @@ struct StreamParams {
     int64_t n_info, T, f, v;
     int64_t n_win, n_pairs;
     uint32_t flags;         // bit0: terminated, bit1: start state unknown
-    int32_t wpad_max;       // padded frame length used as the scratch stage stride
+    int32_t wpad_max;       // padded frame length the scratch of one warp holds
     uint32_t *out;          // packed decoded bits, LSB-first
-    uint32_t *surv;         // survivor scratch
+    uint32_t *surv;         // survivor scratch: wpad_max x 32 x NW words per warp
     int32_t *pm_out;        // optional [n_win][2^(K-1)] canonical final metrics
+    int *status;            // device status word (bit 0: a frame pair exceeded the scratch)
 };
+
+// One frame as the decoder core sees it: stage indices are relative to the
+// first stage of its stream (or packet), whose LLRs start at llr and whose
+// decoded bits start at bit 0 of out.
+struct FrameTask {
+    const int8_t *llr;      // [T][beta] int8 of the frame's stream
+    uint32_t *out;          // packed output of the frame's stream
+    int32_t *pm;            // NULL, or 2^(K-1) canonical final metrics of this frame
+    int64_t a, b, o, e;     // trellis stages [a, b), decoded stages [o, e)
+    int valid, known, term; // real frame / starts from state 0 / ends at a terminated end
+};
+
+__host__ __device__ __forceinline__ FrameTask frame_task(const int8_t *llr, uint32_t *out, int32_t *pm,
+                                                        int64_t s, int64_t n_win, int64_t n_info,
+                                                        int64_t T, int64_t f, int64_t v,
+                                                        uint32_t flags) {
+    FrameTask t;
+    t.llr = llr;
+    t.out = out;
+    t.valid = s < n_win;
+    const Frame w = frame_of(t.valid ? s : 0, n_info, T, f, v, flags);
+    t.a = w.a; t.b = w.b; t.o = w.o; t.e = w.e;
+    t.known = t.valid && w.known_start;
+    t.term = t.valid && w.term_end;
+    t.pm = t.valid ? pm : nullptr;
+    return t;
+}
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
@@ -141,8 +169,13 @@ __host__ __device__ constexpr uint32_t bitk_mask(int k) {
          : k == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
-template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
-__global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
+// Forward procedure, survivor storage and traceback for one pair of frames.
+// Called by one group of L lanes; surv is this warp's scratch (wpad_cap
+// stages x 32 lanes x NW words); wlane is the lane in the warp.
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4>
+__device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *surv, int wpad_cap,
+                                            int wlane, int lane, unsigned gmask, int grp_base,
+                                            int *status) {
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     using C = typename Cfg::C;
     constexpr int NB = Cfg::NB, NR = Cfg::NR, LR = Cfg::LR, U = Cfg::U, UW = Cfg::UW;
@@ -152,31 +185,24 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     constexpr uint32_t SEED0 = (uint32_t)(Cfg::F + C::S) * 0x00010001u;  // state 0 after a reset
     constexpr uint32_t SEEDX = (uint32_t)Cfg::F * 0x00010001u;           // other states after a reset
 
-    const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
-    const int64_t q = gtid / L;
-    const int lane = (int)(gtid % L);
-    if (q >= p.n_pairs) return;   // whole lane groups leave together
-    const unsigned warp_lane = threadIdx.x & 31u;
-    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu
-                                     : (((1u << L) - 1u) << (warp_lane & ~(unsigned)(L - 1)));
-    const int grp_base = (int)(warp_lane & ~(unsigned)(L - 1));
-
     // ---------------------------------------------------------- frame plan
     int64_t fa[2], fb[2], fo[2], fe[2];
     bool known[2], term[2], valid[2];
     int64_t W[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int64_t s = 2 * q + h;
-        valid[h] = s < p.n_win;
-        Frame w = frame_of(valid[h] ? s : 0, p.n_info, p.T, p.f, p.v, p.flags);
-        fa[h] = w.a; fb[h] = w.b; fo[h] = w.o; fe[h] = w.e;
-        known[h] = valid[h] && w.known_start;
-        term[h] = valid[h] && w.term_end;
-        W[h] = valid[h] ? (w.b - w.a) : 0;
+        fa[h] = ft[h].a; fb[h] = ft[h].b; fo[h] = ft[h].o; fe[h] = ft[h].e;
+        valid[h] = ft[h].valid != 0;
+        known[h] = ft[h].known != 0;
+        term[h] = ft[h].term != 0;
+        W[h] = valid[h] ? (fb[h] - fa[h]) : 0;
     }
     const int64_t Wmax = W[0] > W[1] ? W[0] : W[1];
     const int Wpad = (int)(((Wmax + U - 1) / U) * U);
+    if (Wpad > wpad_cap) {   // never happens for plans built by the host; refuse, do not overrun
+        if (lane == 0) atomicOr(status, 1);
+        return;
+    }
     int tau0[2], tauo[2], taue[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -205,13 +231,12 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) P[r] = SEED0;   // all-equal: unknown start
 
-    uint32_t *const surv_blk = p.surv + (size_t)blockIdx.x * (size_t)p.wpad_max * NT * NW;
     const int64_t vb0 = (fa[0] - tau0[0]) * BETA, vb1 = (fa[1] - tau0[1]) * BETA;
     const int64_t lo0 = fa[0] * BETA, hi0 = valid[0] ? fb[0] * BETA : lo0;
     const int64_t lo1 = fa[1] * BETA, hi1 = valid[1] ? fb[1] * BETA : lo1;
 
     auto store_words = [&](int tau, const uint32_t (&wd)[NW]) {
-        uint32_t *dst = surv_blk + ((size_t)tau * NT + threadIdx.x) * NW;
+        uint32_t *dst = surv + ((size_t)tau * 32 + wlane) * NW;
         if constexpr (NW == 1) {
             *dst = wd[0];
         } else if constexpr (NW == 2) {
@@ -226,8 +251,8 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     const int nchunks = Wpad / U;
     for (int c = 0; c < nchunks; ++c) {
         uint32_t cw0[UW], cw1[UW];
-        load_chunk<UW>(p.llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cw0);
-        load_chunk<UW>(p.llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cw1);
+        load_chunk<UW>(ft[0].llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cw0);
+        load_chunk<UW>(ft[1].llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cw1);
         uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
 
         static_for<U>([&](auto Sc) {
@@ -448,7 +473,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     }
 
     // optional canonical final metrics (lambda - min lambda), for parity checks
-    if (p.pm_out) {
+    if (ft[0].pm || ft[1].pm) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t mn = 0xFFFFu;
@@ -464,8 +489,8 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
                     mn = mn < o ? mn : o;
                 }
             }
-            if (valid[h]) {
-                int32_t *dst = p.pm_out + (2 * q + h) * (int64_t)C::NS + ((int64_t)lane << LR);
+            if (ft[h].pm) {
+                int32_t *dst = ft[h].pm + ((int64_t)lane << LR);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
@@ -484,7 +509,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     constexpr int G = NB;
     uint32_t oacc[2] = {0u, 0u};
     const int64_t toff0 = fa[0] - tau0[0], toff1 = fa[1] - tau0[1];
-    const uint32_t *my = surv_blk + (size_t)threadIdx.x * NW;
+    const uint32_t *my = surv + (size_t)wlane * NW;
 
     auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
         // bit of register Rh of frame h in this lane's words for one stage
@@ -507,7 +532,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
             oacc[h] = (oacc[h] << 1) | u;
             const int64_t tabs = (int64_t)t + (h ? toff1 : toff0);
             if ((tabs & 31) == 0) {
-                if (lane == (L > 1 ? h : 0)) p.out[tabs >> 5] = oacc[h];
+                if (lane == (L > 1 ? h : 0)) ft[h].out[tabs >> 5] = oacc[h];
                 oacc[h] = 0;
             }
         }
@@ -518,7 +543,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int t = t0 - g;
-            const uint32_t *src = my + (size_t)t * NT * NW;
+            const uint32_t *src = my + (size_t)t * 32 * NW;
             if (t >= tau_store) {
                 if constexpr (NW == 1) {
                     buf[g][0] = __ldg(src);
@@ -596,6 +621,29 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
             if (t0 < tau_store) break;
         }
     }
+}
+
+// Segmented decode of one stream: frame pair q = (2q, 2q+1) per group of L lanes.
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+__global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
+    constexpr int NS = 1 << (K - 1);
+    const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t q = gtid / L;
+    const int lane = (int)(gtid % L);
+    if (q >= p.n_pairs) return;   // whole lane groups leave together
+    const int wlane = (int)(threadIdx.x & 31u);
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
+    const int grp_base = wlane & ~(L - 1);
+    FrameTask ft[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t s = 2 * q + h;
+        ft[h] = frame_task(p.llr, p.out, p.pm_out ? p.pm_out + s * NS : nullptr, s, p.n_win,
+                           p.n_info, p.T, p.f, p.v, p.flags);
+    }
+    uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u *
+                                  (size_t)StreamCfg<K, BETA, GENS, L, RADIX4>::NW;
+    decode_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status);
 }
 
 }  // namespace vd
