@@ -142,6 +142,39 @@ vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_
  */
 vd_status vd_sync(void *stream);
 
+/*
+ * vd_decode_noalloc — the stream decode of vd_decode without any device
+ * allocation.  The paper has no counterpart: this is a deployment variant.
+ *
+ * For callers that must not allocate device memory while they run: a
+ * real-time receiver thread that cannot absorb the latency of cudaMalloc (it
+ * can block and synchronise the device), a program whose device memory is
+ * reserved up front by another allocator or a fixed budget, or a process that
+ * must not grow after start-up.  This call makes no allocation at all (no
+ * cudaMalloc, cudaFree or allocating library routine); the caller passes the
+ * input and output buffers as for vd_decode.
+ *
+ * Survivor scratch: a file-scope device array of vd_noalloc_scratch_limit()
+ * bytes (32 MiB), which occupies that much memory on every GPU where the
+ * library's device code is loaded, until the process exits.  A stream whose
+ * scratch would not fit is rejected with VD_EINVAL and a message giving both
+ * sizes (for the K=7 code at f=256, v=42 this is about 3 million info bits).
+ *
+ * Arguments as vd_decode, restricted to unpunctured int8 LLRs (VD_LLR_S8);
+ * no metric output.  The first call on each device looks up the device
+ * address of the array (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array: calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race on it and corrupt each other's results;
+ * serialise them (one stream).  A status word in a second static array is
+ * cleared by every call.
+ */
+vd_status vd_decode_noalloc(const vd_code *code, const void *d_llr, int64_t n_info, int f, int v,
+                            int radix, uint32_t flags, uint32_t *d_out, void *stream);
+
+/* Size in bytes of the fixed survivor scratch used by vd_decode_noalloc. */
+int64_t vd_noalloc_scratch_limit(void);
+
 /* Number of frames of a stream decode: ceil(n_info / f) (0 if n_info <= 0). */
 int64_t vd_num_frames(int64_t n_info, int f);
 

@@ -21,7 +21,7 @@ __all__ = [
     "VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_EUNSUPPORTED", "VD_ETIMEOUT", "VD_EBOUNDS",
     "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_TERMINATED", "VD_START_UNKNOWN",
     "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
-    "vd_decode", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_decode", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -79,6 +79,10 @@ def lib():
         L.vd_num_kept.restype = i64
         L.vd_scratch_bytes.argtypes = [vp, i64, i32, i32, i32, P(VdTune)]
         L.vd_scratch_bytes.restype = i64
+        L.vd_decode_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, u32, vp, vp]
+        L.vd_decode_noalloc.restype = i32
+        L.vd_noalloc_scratch_limit.argtypes = []
+        L.vd_noalloc_scratch_limit.restype = i64
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -183,6 +187,21 @@ def vd_decode(handle, llr, llr_type, n_info, f, v, radix, flags, out, pm=None, t
                            ctypes.c_void_p(pm.data_ptr()) if pm is not None else None,
                            ctypes.byref(tune) if tune is not None else None,
                            _stream_handle(stream)))
+
+
+def vd_decode_noalloc(handle, llr, n_info, f, v, radix, flags, out, stream=None):
+    """Calls vd_decode_noalloc: the stream decode with no device allocation
+    (fixed scratch of vd_noalloc_scratch_limit() bytes; int8, unpunctured)."""
+    for name, t in (("llr", llr), ("out", out)):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    _check(lib().vd_decode_noalloc(ctypes.c_void_p(handle), ctypes.c_void_p(llr.data_ptr()),
+                                   int(n_info), int(f), int(v), int(radix), int(flags),
+                                   ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+
+def vd_noalloc_scratch_limit() -> int:
+    return int(lib().vd_noalloc_scratch_limit())
 
 
 class Code:
