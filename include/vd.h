@@ -135,6 +135,82 @@ vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_
                     int f, int v, int radix, uint32_t flags, uint32_t *d_out, int32_t *d_pm,
                     const vd_tune *tune, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ *
+ * Many packets (terminated or not, of up to 16 codes, punctured or not,
+ * int8 or 4-bit) decoded by one persistent launch per code kind.  Every frame
+ * of every packet is cut as in vd_decode (Sec. III); the frames are sorted by
+ * length, paired, and pulled by resident warps longest first.  The paper has
+ * no batch API; this is the data-parallel form of its frame decoding applied
+ * across packets.
+ */
+typedef struct vd_packet {
+    int32_t code_id;         /* index into the codes array */
+    int32_t llr_type;        /* VD_LLR_S8 or VD_LLR_S4 */
+    int64_t llr_offset;      /* first received value of the packet in the LLR arena, counted in
+                                values (bytes for int8, nibbles for 4-bit; must be even then) */
+    int64_t n_info;          /* information bits, > 0 */
+    uint32_t flags;          /* VD_TERMINATED, VD_START_UNKNOWN */
+    int32_t f;               /* frame length; 0 = chosen by the library (then v is too) */
+    int32_t v;               /* overlap on each side (used when f > 0) */
+    int32_t reserved;
+    int64_t out_word_offset; /* first uint32 word of the packet's decoded bits in the output arena */
+} vd_packet;
+
+typedef struct vd_batch_plan vd_batch_plan;   /* opaque, owns device memory */
+
+typedef struct vd_batch_info {
+    int64_t n_packets, n_frames, n_pairs;
+    int64_t scratch_bytes;       /* survivor + depunctured-LLR device memory held by the plan */
+    int64_t resident_warps;      /* persistent warps per launch (last code kind) */
+    int32_t lanes, radix;        /* kernel shape (last code kind) */
+    int32_t n_launches;          /* kernel launches per vd_batch_plan_launch */
+    int32_t reserved;
+} vd_batch_info;
+
+/*
+ * Builds a batch plan: checks every descriptor on the host, chooses f and v
+ * for packets with f == 0 (one frame length per code kind that minimises the
+ * predicted makespan of the persistent launch; packets no longer than it are
+ * decoded as one full-length frame; v = 42 for K=7, 64 for K=9, or tune->v),
+ * sorts and pairs all frames, and uploads descriptors and work list (device
+ * memory owned by the plan).  tune: NULL, or lanes / radix / f / v overrides.
+ * The arenas are given at launch.  Synchronises `stream` before returning.
+ */
+vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *const *codes, int n_codes,
+                               const vd_packet *packets, int64_t n_packets, const vd_tune *tune,
+                               void *stream);
+
+/* Launches the plan on `stream`: the input pre-pass (if any packet is
+ * punctured or 4-bit), then one persistent kernel per code kind.  d_llr_arena
+ * holds every packet's received values at its llr_offset; d_out_arena receives
+ * the packed bits at each packet's out_word_offset (ceil(n_info/32) words;
+ * packets must not share words).  Asynchronous. */
+vd_status vd_batch_plan_launch(vd_batch_plan *plan, const void *d_llr_arena, uint32_t *d_out_arena,
+                               void *stream);
+
+/* Same as vd_batch_plan_launch, through a CUDA graph captured on the first call
+ * for these arenas and replayed afterwards.  Needs a non-default stream. */
+vd_status vd_batch_plan_launch_graph(vd_batch_plan *plan, const void *d_llr_arena,
+                                     uint32_t *d_out_arena, void *stream);
+
+/* Sizes and shape of a plan. */
+vd_status vd_batch_plan_info(const vd_batch_plan *plan, vd_batch_info *info);
+
+/* The f and v used for each packet (arrays of n_packets). */
+vd_status vd_batch_plan_packet_tune(const vd_batch_plan *plan, int32_t *f_out, int32_t *v_out);
+
+/* Waits for `stream`; VD_EBOUNDS if a launch of this plan refused work. */
+vd_status vd_batch_plan_status(vd_batch_plan *plan, void *stream);
+
+/* Frees a plan after the device is idle (NULL is ignored). */
+void vd_batch_plan_destroy(vd_batch_plan *plan);
+
+/* One-shot batch decode: plan, launch, wait for `stream`, free. */
+vd_status vd_decode_batch(const vd_code *const *codes, int n_codes, const vd_packet *packets,
+                          int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena,
+                          const vd_tune *tune, void *stream);
+
 /*
  * Waits for the stream, then reads and clears the library's device status
  * word.  VD_EBOUNDS if a kernel refused work that would have overrun its

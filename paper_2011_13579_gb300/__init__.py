@@ -21,7 +21,9 @@ __all__ = [
     "VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_EUNSUPPORTED", "VD_ETIMEOUT", "VD_EBOUNDS",
     "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_TERMINATED", "VD_START_UNKNOWN",
     "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
-    "vd_decode", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_decode", "vd_decode_batch", "vd_batch_plan_create", "vd_batch_plan_launch",
+    "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
+    "VdPacket", "VdBatchInfo", "BatchPlan", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -43,6 +45,21 @@ class VdTune(ctypes.Structure):
     _fields_ = [("f", ctypes.c_int32), ("v", ctypes.c_int32), ("radix", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 3)]
+
+
+class VdPacket(ctypes.Structure):
+    _fields_ = [("code_id", ctypes.c_int32), ("llr_type", ctypes.c_int32),
+                ("llr_offset", ctypes.c_int64), ("n_info", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("f", ctypes.c_int32), ("v", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("out_word_offset", ctypes.c_int64)]
+
+
+class VdBatchInfo(ctypes.Structure):
+    _fields_ = [("n_packets", ctypes.c_int64), ("n_frames", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+                ("resident_warps", ctypes.c_int64), ("lanes", ctypes.c_int32),
+                ("radix", ctypes.c_int32), ("n_launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -83,6 +100,22 @@ def lib():
         L.vd_decode_noalloc.restype = i32
         L.vd_noalloc_scratch_limit.argtypes = []
         L.vd_noalloc_scratch_limit.restype = i64
+        L.vd_batch_plan_create.argtypes = [P(vp), P(vp), i32, P(VdPacket), i64, P(VdTune), vp]
+        L.vd_batch_plan_create.restype = i32
+        L.vd_batch_plan_launch.argtypes = [vp, vp, vp, vp]
+        L.vd_batch_plan_launch.restype = i32
+        L.vd_batch_plan_launch_graph.argtypes = [vp, vp, vp, vp]
+        L.vd_batch_plan_launch_graph.restype = i32
+        L.vd_batch_plan_info.argtypes = [vp, P(VdBatchInfo)]
+        L.vd_batch_plan_info.restype = i32
+        L.vd_batch_plan_packet_tune.argtypes = [vp, P(ctypes.c_int32), P(ctypes.c_int32)]
+        L.vd_batch_plan_packet_tune.restype = i32
+        L.vd_batch_plan_status.argtypes = [vp, vp]
+        L.vd_batch_plan_status.restype = i32
+        L.vd_batch_plan_destroy.argtypes = [vp]
+        L.vd_batch_plan_destroy.restype = None
+        L.vd_decode_batch.argtypes = [P(vp), i32, P(VdPacket), i64, vp, vp, P(VdTune), vp]
+        L.vd_decode_batch.restype = i32
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -202,6 +235,108 @@ def vd_decode_noalloc(handle, llr, n_info, f, v, radix, flags, out, stream=None)
 
 def vd_noalloc_scratch_limit() -> int:
     return int(lib().vd_noalloc_scratch_limit())
+
+
+def _packet_array(packets):
+    """packets: a ctypes VdPacket array, or a dict of equal-length numpy arrays
+    with keys code_id, llr_type, llr_offset, n_info, flags, f, v, out_word_offset."""
+    if isinstance(packets, ctypes.Array):
+        return packets, len(packets)
+    import numpy as np
+    n = len(packets["n_info"])
+    dt = np.dtype([("code_id", "<i4"), ("llr_type", "<i4"), ("llr_offset", "<i8"), ("n_info", "<i8"),
+                   ("flags", "<u4"), ("f", "<i4"), ("v", "<i4"), ("reserved", "<i4"),
+                   ("out_word_offset", "<i8")])
+    assert dt.itemsize == ctypes.sizeof(VdPacket)
+    rec = np.zeros(n, dtype=dt)
+    for k in ("code_id", "llr_type", "llr_offset", "n_info", "flags", "f", "v", "out_word_offset"):
+        if k in packets:
+            rec[k] = packets[k]
+    arr = (VdPacket * n).from_buffer_copy(rec.tobytes()) if n else (VdPacket * 0)()
+    return arr, n
+
+
+def _code_handles(codes):
+    hs = [c.handle if isinstance(c, Code) else c for c in codes]
+    return (ctypes.c_void_p * len(hs))(*hs)
+
+
+def vd_batch_plan_create(codes, packets, tune=None, stream=None):
+    arr, n = _packet_array(packets)
+    h = ctypes.c_void_p()
+    _check(lib().vd_batch_plan_create(ctypes.byref(h), _code_handles(codes), len(codes), arr, n,
+                                      ctypes.byref(tune) if tune is not None else None,
+                                      _stream_handle(stream)))
+    return h.value
+
+
+def vd_batch_plan_launch(plan, llr_arena, out_arena, stream=None, graph=False):
+    fn = lib().vd_batch_plan_launch_graph if graph else lib().vd_batch_plan_launch
+    _check(fn(ctypes.c_void_p(plan), ctypes.c_void_p(llr_arena.data_ptr()),
+              ctypes.c_void_p(out_arena.data_ptr()), _stream_handle(stream)))
+
+
+def vd_batch_plan_info(plan) -> VdBatchInfo:
+    info = VdBatchInfo()
+    _check(lib().vd_batch_plan_info(ctypes.c_void_p(plan), ctypes.byref(info)))
+    return info
+
+
+def vd_batch_plan_packet_tune(plan, n_packets):
+    import numpy as np
+    f = np.zeros(n_packets, dtype=np.int32)
+    v = np.zeros(n_packets, dtype=np.int32)
+    _check(lib().vd_batch_plan_packet_tune(ctypes.c_void_p(plan),
+                                           f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return f, v
+
+
+def vd_batch_plan_status(plan, stream=None) -> None:
+    _check(lib().vd_batch_plan_status(ctypes.c_void_p(plan), _stream_handle(stream)))
+
+
+def vd_batch_plan_destroy(plan) -> None:
+    if plan:
+        lib().vd_batch_plan_destroy(ctypes.c_void_p(plan))
+
+
+def vd_decode_batch(codes, packets, llr_arena, out_arena, tune=None, stream=None):
+    arr, n = _packet_array(packets)
+    _check(lib().vd_decode_batch(_code_handles(codes), len(codes), arr, n,
+                                 ctypes.c_void_p(llr_arena.data_ptr()),
+                                 ctypes.c_void_p(out_arena.data_ptr()),
+                                 ctypes.byref(tune) if tune is not None else None,
+                                 _stream_handle(stream)))
+
+
+class BatchPlan:
+    """Owning wrapper of a vd_batch_plan."""
+
+    def __init__(self, codes, packets, tune=None, stream=None):
+        self.codes = list(codes)
+        self.n_packets = len(packets["n_info"]) if isinstance(packets, dict) else len(packets)
+        self.handle = vd_batch_plan_create(self.codes, packets, tune=tune, stream=stream)
+
+    def launch(self, llr_arena, out_arena, stream=None, graph=False):
+        vd_batch_plan_launch(self.handle, llr_arena, out_arena, stream=stream, graph=graph)
+
+    def info(self):
+        return vd_batch_plan_info(self.handle)
+
+    def packet_tune(self):
+        return vd_batch_plan_packet_tune(self.handle, self.n_packets)
+
+    def status(self, stream=None):
+        vd_batch_plan_status(self.handle, stream)
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            vd_batch_plan_destroy(h)
+
+    def __del__(self):
+        self.close()
 
 
 class Code:

@@ -1,0 +1,87 @@
+// Persistent batched decode: many packets (or streams) of one code kind in
+// one launch.  The host sorts every frame of every packet by length, pairs
+// neighbours, and groups 32/L pairs into a warp task; resident warps pull
+// tasks from a global counter (longest first) and run the same frame-pair
+// decoder as the stream kernel (decode_pair) on each.
+#pragma once
+#include "vd_stream.cuh"
+
+namespace vd {
+
+// Device-side packet descriptor (offsets are relative to the launch's arenas).
+struct PacketDesc {
+    int64_t llr_off;        // byte offset of the packet's int8 [T][beta] LLRs
+    int64_t out_word_off;   // word offset of the packet's decoded bits
+    int64_t n_info;
+    int32_t f, v;
+    uint32_t flags;         // VD_TERMINATED / VD_START_UNKNOWN; bit 31: LLRs in the internal arena
+    int32_t reserved;
+};
+
+constexpr uint32_t PKT_INTERNAL_LLR = 0x80000000u;
+
+// One frame pair: packet and frame index of each half (packet ~0u: no frame).
+struct PairRef {
+    uint32_t p0, s0, p1, s1;
+};
+
+struct BatchParams {
+    const PacketDesc *pk;
+    const PairRef *pairs;     // sorted; warp task t covers pairs [t * 32/L, (t+1) * 32/L)
+    int64_t n_pairs, n_tasks;
+    const int8_t *llr_user;   // the caller's arena (unpunctured int8 packets)
+    const int8_t *llr_int;    // the internal arena (depunctured / unpacked packets)
+    uint32_t *out;            // the caller's output arena
+    int *counter;             // task counter, zero at launch
+    uint32_t *surv;           // per resident warp: wpad_cap x 32 x NW words
+    int32_t wpad_cap;
+    int *status;
+};
+
+template <int K>
+__device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t pk, uint32_t s) {
+    FrameTask t;
+    if (pk == 0xFFFFFFFFu) {
+        t = frame_task(p.llr_user, p.out, nullptr, 1, 0, 1, 1, 1, 0, 0);   // invalid frame
+        return t;
+    }
+    const PacketDesc d = p.pk[pk];
+    const uint32_t fl = d.flags & ~PKT_INTERNAL_LLR;
+    const int64_t T = d.n_info + ((fl & 1u) ? K - 1 : 0);
+    const int64_t n_win = (d.n_info + d.f - 1) / d.f;
+    const int8_t *llr = ((d.flags & PKT_INTERNAL_LLR) ? p.llr_int : p.llr_user) + d.llr_off;
+    return frame_task(llr, p.out + d.out_word_off, nullptr, (int64_t)s, n_win, d.n_info, T, d.f, d.v, fl);
+}
+
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+__global__ void __launch_bounds__(NT) batch_kernel(const BatchParams p) {
+    constexpr int PPW = 32 / L;
+    constexpr int NW = StreamCfg<K, BETA, GENS, L, RADIX4>::NW;
+    const int wlane = (int)(threadIdx.x & 31u);
+    const int group = wlane / L;
+    const int lane = wlane % L;
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
+    const int grp_base = wlane & ~(L - 1);
+    const int64_t gwarp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    uint32_t *surv = p.surv + (size_t)gwarp * (size_t)p.wpad_cap * 32u * (size_t)NW;
+    while (true) {
+        int t = 0;
+        if (wlane == 0) t = atomicAdd(p.counter, 1);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (t >= p.n_tasks) break;
+        const int64_t pi = (int64_t)t * PPW + group;
+        FrameTask ft[2];
+        if (pi < p.n_pairs) {
+            const PairRef r = p.pairs[pi];
+            ft[0] = packet_frame<K>(p, r.p0, r.s0);
+            ft[1] = packet_frame<K>(p, r.p1, r.s1);
+        } else {
+            ft[0] = packet_frame<K>(p, 0xFFFFFFFFu, 0);
+            ft[1] = ft[0];
+        }
+        decode_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_cap, wlane, lane, gmask, grp_base, p.status);
+        __syncwarp();   // the next task reuses this warp's scratch
+    }
+}
+
+}  // namespace vd

@@ -2,7 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
-#include "vd_stream.cuh"
+#include "vd_batch.cuh"
 
 namespace vd {
 
@@ -28,6 +28,12 @@ cudaError_t launch_stream_k7(int lanes, bool radix4, const StreamParams &p, int6
                              cudaStream_t st);
 cudaError_t launch_stream_k9(int lanes, bool radix4, const StreamParams &p, int64_t blocks,
                              cudaStream_t st);
+cudaError_t launch_batch_k7(int lanes, bool radix4, const BatchParams &p, int64_t blocks,
+                            cudaStream_t st);
+cudaError_t launch_batch_k9(int lanes, bool radix4, const BatchParams &p, int64_t blocks,
+                            cudaStream_t st);
+cudaError_t batch_occupancy_k7(int lanes, bool radix4, int *blocks_per_sm);
+cudaError_t batch_occupancy_k9(int lanes, bool radix4, int *blocks_per_sm);
 bool geom_k7(int lanes, bool radix4, KernelGeom *g);
 bool geom_k9(int lanes, bool radix4, KernelGeom *g);
 
