@@ -62,6 +62,16 @@ __device__ __forceinline__ uint32_t max_s16x2(uint32_t a, uint32_t b) {
 __device__ __forceinline__ uint32_t addmax_u16x2(uint32_t a, uint32_t b, uint32_t c) {
     return max_u16x2(add_u16x2(a, b), c);
 }
+// a * b + c on the FMA pipe (IMAD).  Callers pass b = +1 / -1 held in a
+// register whose value the compiler cannot know, so the multiply-add stays an
+// IMAD instead of becoming an ALU-pipe add.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// per-half two's-complement negation (no 16x2 subtract exists)
+__device__ __forceinline__ uint32_t neg_s16x2(uint32_t x) { return add_u16x2(~x, 0x00010001u); }
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t d;
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));

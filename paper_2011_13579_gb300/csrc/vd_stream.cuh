@@ -124,22 +124,42 @@ __device__ __forceinline__ void static_for(Fn &&fn) {
     static_for_impl(fn, std::make_integer_sequence<int, N>{});
 }
 
-// Loads bytes [vb, vb + 4*UW) of the LLR stream as UW words, zero outside [lo, hi).
+// LLR chunk loading in two steps so the loads of chunk c+1 are in flight while
+// chunk c is decoded: fetch() issues the aligned 32-bit loads of bytes
+// [vb, vb + 4*UW) of the stream, finish() re-aligns them with funnel shifts.
+// A chunk that is not wholly inside [lo, hi) (the first chunk of a padded
+// frame, or a frame at a stream edge) is assembled byte by byte in finish()
+// with zeros outside the range.
 template <int UW>
-__device__ __forceinline__ void load_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
-                                           uint32_t (&w)[UW]) {
-    if (vb >= lo && vb + 4 * UW <= hi) {
+struct ChunkRaw {
+    uint32_t raw[UW + 1];
+    uint32_t sh;
+    bool fast;
+};
+
+template <int UW>
+__device__ __forceinline__ void fetch_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
+                                            ChunkRaw<UW> &c) {
+    c.fast = vb >= lo && vb + 4 * UW <= hi;
+    if (c.fast) {
         const uintptr_t addr = reinterpret_cast<uintptr_t>(llr) + (uintptr_t)vb;
         const uint32_t mis = (uint32_t)(addr & 3u);
         const uint32_t *p = reinterpret_cast<const uint32_t *>(addr - mis);
-        uint32_t raw[UW + 1];
 #pragma unroll
-        for (int i = 0; i < UW; ++i) raw[i] = __ldg(p + i);
+        for (int i = 0; i < UW; ++i) c.raw[i] = __ldg(p + i);
         // the extra word holds the last bytes of the chunk when it is misaligned;
         // it contains at least one byte inside the stream, so it is readable
-        raw[UW] = mis ? __ldg(p + UW) : 0u;
+        c.raw[UW] = mis ? __ldg(p + UW) : 0u;
+        c.sh = 8u * mis;
+    }
+}
+
+template <int UW>
+__device__ __forceinline__ void finish_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
+                                             const ChunkRaw<UW> &c, uint32_t (&w)[UW]) {
+    if (c.fast) {
 #pragma unroll
-        for (int i = 0; i < UW; ++i) w[i] = funnel_r(raw[i], raw[i + 1], 8u * mis);
+        for (int i = 0; i < UW; ++i) w[i] = funnel_r(c.raw[i], c.raw[i + 1], c.sh);
     } else {
 #pragma unroll
         for (int i = 0; i < UW; ++i) {
@@ -167,6 +187,141 @@ __device__ __forceinline__ uint32_t pick(const uint32_t *a, uint32_t idx) {
 __host__ __device__ constexpr uint32_t bitk_mask(int k) {
     return k == 0 ? 0xAAAAAAAAu : k == 1 ? 0xCCCCCCCCu : k == 2 ? 0xF0F0F0F0u
          : k == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+
+// Backward procedure (Algorithm 2) for one pair of frames, from the final
+// registers R[h] (frame h's traceback start, in register space) down to each
+// frame's first decoded stage.  Every lane of the group follows both frames;
+// the lane that owns the current register supplies the decision bit (one
+// shuffle).  Stages are walked in groups of K-1 starting at Wpad-1, so the
+// phase of every stage in a group is a compile-time constant; the next
+// group's survivor words are loaded while the current group is walked.
+// Survivor words: bit (r & 31) of word (r >> 5) holds register r of the lane
+// (r & 15 at bit 16h when a lane has 16 registers or fewer), frame 0 first.
+template <int K, int L, bool RADIX4, int NR, int NW>
+__device__ __forceinline__ void traceback_pair(const FrameTask (&ft)[2], const uint32_t *surv,
+                                               uint32_t (&R)[2], const int (&tauo)[2],
+                                               const int (&taue)[2], const int64_t (&toff)[2],
+                                               int tau_store, int Wpad, int wlane, int lane,
+                                               unsigned gmask, int grp_base) {
+    constexpr int NB = K - 1;
+    constexpr int LR = ilog2(NR);
+    constexpr int WPF = NR >= 32 ? NR / 32 : 1;
+    constexpr int G = NB;
+    uint32_t oacc[2] = {0u, 0u};
+    const uint32_t *my = surv + (size_t)wlane * NW;
+
+    auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
+        // bit of register Rh of frame h in this lane's words for one stage
+        uint32_t word, bit;
+        if constexpr (NR >= 32) {
+            word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
+            bit = Rh & 31u;
+        } else {
+            word = wd[0];
+            bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
+        }
+        return (word >> bit) & 1u;
+    };
+    auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
+        if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
+        else return bits;
+    };
+    auto emit = [&](int h, int t, uint32_t u) {
+        if (t < taue[h]) {
+            oacc[h] = (oacc[h] << 1) | u;
+            const int64_t tabs = (int64_t)t + toff[h];
+            if ((tabs & 31) == 0) {
+                if (lane == (L > 1 ? h : 0)) ft[h].out[tabs >> 5] = oacc[h];
+                oacc[h] = 0;
+            }
+        }
+    };
+
+    uint32_t bufA[G][NW], bufB[G][NW];
+    auto load_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int t = t0 - g;
+            const uint32_t *src = my + (size_t)t * 32 * NW;
+            if (t >= tau_store) {
+                if constexpr (NW == 1) {
+                    buf[g][0] = __ldg(src);
+                } else if constexpr (NW == 2) {
+                    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(src));
+                    buf[g][0] = x.x; buf[g][1] = x.y;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NW; i += 4) {
+                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + i));
+                        buf[g][i] = x.x; buf[g][i + 1] = x.y; buf[g][i + 2] = x.z; buf[g][i + 3] = x.w;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) buf[g][i] = 0u;
+            }
+        }
+    };
+    auto walk_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+        if constexpr (!RADIX4) {
+            static_for<G>([&](auto gc) {
+                constexpr int g = decltype(gc)::value;
+                constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // t0 = -1 mod (K-1)
+                const int t = t0 - g;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (t >= tauo[h]) {
+                        const uint32_t d = owner_bits(decision(buf[g], h, R[h]), R[h]);
+                        const uint32_t u = (R[h] >> ph) & 1u;
+                        R[h] = (R[h] & ~(1u << ph)) | (d << ph);
+                        emit(h, t, u);
+                    }
+                }
+            });
+        } else {
+            // pairs (t, t-1): t is the second stage of a pair (odd offset in a chunk)
+            static_for<G / 2>([&](auto gc) {
+                constexpr int g = 2 * decltype(gc)::value;
+                constexpr int ph2 = ((NB - 1 - g) % NB + NB) % NB;
+                constexpr int ph1 = ((NB - 2 - g) % NB + NB) % NB;
+                const int t = t0 - g;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (t >= tauo[h]) {
+                        const uint32_t b2 = decision(buf[g], h, R[h]);
+                        const uint32_t b1 = decision(buf[g + 1], h, R[h]);   // same position
+                        const uint32_t bb = owner_bits(b2 | (b1 << 1), R[h]);
+                        const uint32_t u2 = (R[h] >> ph2) & 1u;
+                        const uint32_t m = (R[h] & ~(1u << ph2)) | ((bb & 1u) << ph2);
+                        emit(h, t, u2);
+                        if (t - 1 >= tauo[h]) {
+                            const uint32_t u1 = (m >> ph1) & 1u;
+                            R[h] = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
+                            emit(h, t - 1, u1);
+                        } else {
+                            R[h] = m;
+                        }
+                    }
+                }
+            });
+        }
+    };
+
+    int t0 = Wpad - 1;
+    if (t0 >= tau_store) {
+        load_group(t0, bufA);
+        while (true) {
+            if (t0 - G >= tau_store) load_group(t0 - G, bufB);
+            walk_group(t0, bufA);
+            t0 -= G;
+            if (t0 < tau_store) break;
+            if (t0 - G >= tau_store) load_group(t0 - G, bufA);
+            walk_group(t0, bufB);
+            t0 -= G;
+            if (t0 < tau_store) break;
+        }
+    }
 }
 
 // Forward procedure, survivor storage and traceback for one pair of frames.
@@ -248,11 +403,28 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
         }
     };
 
+    // runtime +1 / -1 for the FMA-pipe multiply-adds (blocks are one-dimensional)
+    const uint32_t one = threadIdx.y + 1u;
+    const uint32_t m1 = 0u - one;
+    constexpr bool COROLLARY = LV == (1u << BETA) - 1u && MV == (1u << BETA) - 1u;
+
     const int nchunks = Wpad / U;
+    ChunkRaw<UW> nx0, nx1;
+    if (nchunks > 0) {
+        fetch_chunk<UW>(ft[0].llr, vb0, lo0, hi0, nx0);
+        fetch_chunk<UW>(ft[1].llr, vb1, lo1, hi1, nx1);
+    }
     for (int c = 0; c < nchunks; ++c) {
         uint32_t cw0[UW], cw1[UW];
-        load_chunk<UW>(ft[0].llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cw0);
-        load_chunk<UW>(ft[1].llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cw1);
+        {
+            const ChunkRaw<UW> cur0 = nx0, cur1 = nx1;
+            if (c + 1 < nchunks) {
+                fetch_chunk<UW>(ft[0].llr, vb0 + (int64_t)(c + 1) * U * BETA, lo0, hi0, nx0);
+                fetch_chunk<UW>(ft[1].llr, vb1 + (int64_t)(c + 1) * U * BETA, lo1, hi1, nx1);
+            }
+            finish_chunk<UW>(ft[0].llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cur0, cw0);
+            finish_chunk<UW>(ft[1].llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cur1, cw1);
+        }
         uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
 
         static_for<U>([&](auto Sc) {
@@ -273,28 +445,52 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
             }
 
             // ---- branch metrics of this stage (Eq. BM), both frames at once
-            uint32_t Lb[BETA];
+            uint32_t Lb[BETA], nLb[BETA];
 #pragma unroll
             for (int b = 0; b < BETA; ++b) {
                 const int j = S * BETA + b;
                 const uint32_t k = (uint32_t)(j & 3);
                 const uint32_t sel = k | ((k + 8u) << 4) | ((k + 4u) << 8) | ((k + 12u) << 12);
                 Lb[b] = prmt(cw0[j >> 2], cw1[j >> 2], sel);   // sign-extended int8 pair
+                nLb[b] = neg_s16x2(Lb[b]);
                 if constexpr (L > 1) {
-                    const uint32_t m = 0u - ((cbits >> (PH * BETA + b)) & 1u);
-                    Lb[b] = sub_s16x2(Lb[b] ^ m, m);
+                    if ((cbits >> (PH * BETA + b)) & 1u) {
+                        const uint32_t t = Lb[b];
+                        Lb[b] = nLb[b];
+                        nLb[b] = t;
+                    }
                 }
             }
             // A[x] = sum_b (-1)^{x_b} l_b for every output pattern x
             uint32_t A[1 << BETA];
             A[0] = Lb[0];
-            A[1] = sub_s16x2(0u, Lb[0]);
+            A[1] = nLb[0];
 #pragma unroll
             for (int b = 1; b < BETA; ++b) {
 #pragma unroll
                 for (int x = 0; x < (1 << b); ++x) {
-                    A[x | (1 << b)] = sub_s16x2(A[x], Lb[b]);
+                    A[x | (1 << b)] = add_s16x2(A[x], nLb[b]);
                     A[x] = add_s16x2(A[x], Lb[b]);
+                }
+            }
+            // decision offsets: E0[a] = d(odd->j0) - d(even->j0) + 0x8000 and
+            // E1[a] = d(odd->j1) - d(even->j1) + 0x8000 per half, for main output a
+            uint32_t E0[1 << BETA], E1[1 << BETA];
+            if constexpr (COROLLARY) {
+                // the odd branches carry the complement pattern: E = 0x8000 + 2 A
+                uint32_t T2[1 << BETA];
+#pragma unroll
+                for (int x = 0; x < (1 << BETA); ++x) T2[x] = add_u16x2(add_s16x2(A[x], A[x]), 0x80008000u);
+#pragma unroll
+                for (int x = 0; x < (1 << BETA); ++x) {
+                    E0[x] = T2[x ^ LV];
+                    E1[x] = T2[x];
+                }
+            } else {
+#pragma unroll
+                for (int x = 0; x < (1 << BETA); ++x) {
+                    E0[x] = add_u16x2(sub_s16x2(A[x ^ LV], A[x]), 0x80008000u);
+                    E1[x] = add_u16x2(sub_s16x2(A[x ^ MV ^ LV], A[x ^ MV]), 0x80008000u);
                 }
             }
 
@@ -309,14 +505,14 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
                 const uint32_t a = C::alpha(C::rotr((uint32_t)ra, PH) >> 1);
                 const uint32_t Pa = P[ra], Pb = P[rb];
                 // even -> j0: alpha, odd -> j0: alpha^LV, even -> j1: alpha^MV, odd -> j1: alpha^MV^LV
-                const uint32_t cb0 = add_u16x2(Pb, A[a ^ LV]);
-                const uint32_t cb1 = add_u16x2(Pb, A[a ^ MV ^ LV]);
-                const uint32_t e0 = add_u16x2(sub_s16x2(A[a ^ LV], A[a]), 0x80008000u);
-                const uint32_t e1 = add_u16x2(sub_s16x2(A[a ^ MV ^ LV], A[a ^ MV]), 0x80008000u);
-                P[ra] = addmax_u16x2(Pa, A[a], cb0);
-                P[rb] = addmax_u16x2(Pa, A[a ^ MV], cb1);
-                X[ra] = Pb - Pa + e0;   // bit 15 / 31 set: odd predecessor wins or ties
-                X[rb] = Pb - Pa + e1;
+                const uint32_t cb0 = add_u16x2(Pb, A[a ^ LV]);        // FMA pipe
+                const uint32_t cb1 = add_u16x2(Pb, A[a ^ MV ^ LV]);   // FMA pipe
+                const uint32_t u = imad(Pa, m1, Pb);                  // Pb - Pa, FMA pipe
+                P[ra] = addmax_u16x2(Pa, A[a], cb0);                  // ALU (fused add + max)
+                P[rb] = addmax_u16x2(Pa, A[a ^ MV], cb1);             // ALU
+                // bit 15 / 31 set: the odd predecessor wins or ties
+                X[ra] = u + E0[a];
+                X[rb] = imad(u, one, E1[a]);
             };
             auto cross = [&](int r) {   // partner register in lane ^ (1 << (PH - LR))
                 constexpr int lb = PH >= LR ? PH - LR : 0;
@@ -328,9 +524,12 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
                 const uint32_t d_oth = xb ? A[a ^ MV] : A[a ^ LV];
                 // holder of R_a: bit = (c_oth >= c_own); holder of R_b: bit = !(c_own >= c_oth),
                 // inverted back after packing
-                const uint32_t e = add_u16x2(sub_s16x2(d_oth, d_own), 0x80008000u) - (xb ? 0x00010001u : 0u);
+                uint32_t e;
+                if constexpr (COROLLARY) e = E0[a];
+                else e = add_u16x2(sub_s16x2(d_oth, d_own), 0x80008000u);
+                e -= xb ? 0x00010001u : 0u;
                 P[r] = addmax_u16x2(own, d_own, add_u16x2(oth, d_oth));
-                X[r] = oth - own + e;
+                X[r] = imad(own, m1, oth) + e;
             };
             auto pack_block = [&](int blk) {   // 16 registers -> acc[blk]
 #pragma unroll
@@ -500,127 +699,9 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
         }
     }
 
-    // -------------------------------------------------------------- traceback
-    // Every lane of the group follows both frames; the lane that owns the
-    // current register supplies the decision bit (one shuffle).  Stages are
-    // walked in groups of K-1 starting at Wpad-1, so the phase of every stage
-    // in a group is a compile-time constant; the next group's survivor words
-    // are loaded while the current group is walked.
-    constexpr int G = NB;
-    uint32_t oacc[2] = {0u, 0u};
-    const int64_t toff0 = fa[0] - tau0[0], toff1 = fa[1] - tau0[1];
-    const uint32_t *my = surv + (size_t)wlane * NW;
-
-    auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
-        // bit of register Rh of frame h in this lane's words for one stage
-        uint32_t word, bit;
-        if constexpr (NR >= 32) {
-            word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
-            bit = Rh & 31u;
-        } else {
-            word = wd[0];
-            bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
-        }
-        return (word >> bit) & 1u;
-    };
-    auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
-        if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
-        else return bits;
-    };
-    auto emit = [&](int h, int t, uint32_t u) {
-        if (t < taue[h]) {
-            oacc[h] = (oacc[h] << 1) | u;
-            const int64_t tabs = (int64_t)t + (h ? toff1 : toff0);
-            if ((tabs & 31) == 0) {
-                if (lane == (L > 1 ? h : 0)) ft[h].out[tabs >> 5] = oacc[h];
-                oacc[h] = 0;
-            }
-        }
-    };
-
-    uint32_t bufA[G][NW], bufB[G][NW];
-    auto load_group = [&](int t0, uint32_t (&buf)[G][NW]) {
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int t = t0 - g;
-            const uint32_t *src = my + (size_t)t * 32 * NW;
-            if (t >= tau_store) {
-                if constexpr (NW == 1) {
-                    buf[g][0] = __ldg(src);
-                } else if constexpr (NW == 2) {
-                    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(src));
-                    buf[g][0] = x.x; buf[g][1] = x.y;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < NW; i += 4) {
-                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + i));
-                        buf[g][i] = x.x; buf[g][i + 1] = x.y; buf[g][i + 2] = x.z; buf[g][i + 3] = x.w;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < NW; ++i) buf[g][i] = 0u;
-            }
-        }
-    };
-    auto walk_group = [&](int t0, uint32_t (&buf)[G][NW]) {
-        if constexpr (!RADIX4) {
-            static_for<G>([&](auto gc) {
-                constexpr int g = decltype(gc)::value;
-                constexpr int ph = NB - 1 - g;     // t0 = -1 mod (K-1)
-                const int t = t0 - g;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (t >= tauo[h]) {
-                        const uint32_t d = owner_bits(decision(buf[g], h, R[h]), R[h]);
-                        const uint32_t u = (R[h] >> ph) & 1u;
-                        R[h] = (R[h] & ~(1u << ph)) | (d << ph);
-                        emit(h, t, u);
-                    }
-                }
-            });
-        } else {
-            // pairs (t, t-1): t is the second stage of a pair (odd offset in a chunk)
-            static_for<G / 2>([&](auto gc) {
-                constexpr int g = 2 * decltype(gc)::value;
-                constexpr int ph2 = NB - 1 - g, ph1 = NB - 2 - g;
-                const int t = t0 - g;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (t >= tauo[h]) {
-                        const uint32_t b2 = decision(buf[g], h, R[h]);
-                        const uint32_t b1 = decision(buf[g + 1], h, R[h]);   // same position
-                        const uint32_t bb = owner_bits(b2 | (b1 << 1), R[h]);
-                        const uint32_t u2 = (R[h] >> ph2) & 1u;
-                        const uint32_t m = (R[h] & ~(1u << ph2)) | ((bb & 1u) << ph2);
-                        emit(h, t, u2);
-                        if (t - 1 >= tauo[h]) {
-                            const uint32_t u1 = (m >> ph1) & 1u;
-                            R[h] = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
-                            emit(h, t - 1, u1);
-                        } else {
-                            R[h] = m;
-                        }
-                    }
-                }
-            });
-        }
-    };
-
-    int t0 = Wpad - 1;
-    if (t0 >= tau_store) {
-        load_group(t0, bufA);
-        while (true) {
-            if (t0 - G >= tau_store) load_group(t0 - G, bufB);
-            walk_group(t0, bufA);
-            t0 -= G;
-            if (t0 < tau_store) break;
-            if (t0 - G >= tau_store) load_group(t0 - G, bufA);
-            walk_group(t0, bufB);
-            t0 -= G;
-            if (t0 < tau_store) break;
-        }
-    }
+    const int64_t toff[2] = {fa[0] - tau0[0], fa[1] - tau0[1]};
+    traceback_pair<K, L, RADIX4, NR, NW>(ft, surv, R, tauo, taue, toff, tau_store, Wpad, wlane, lane,
+                                         gmask, grp_base);
 }
 
 // Segmented decode of one stream: frame pair q = (2q, 2q+1) per group of L lanes.
