@@ -34,11 +34,27 @@ EBN0S = (1.0, 2.0, 3.0, 4.0, 5.0, 6.0)
 K, BETA = 7, 2
 
 
-def workload_config(radix, lanes):
+def workload_config(radix, lanes, path="batch"):
     return {"workload": "segmented stream decode, K=7 r1/2 (171,133), 6 streams x 2^24 info bits, "
                         "Eb/N0 1..6 dB, f=256, v=42, int8 LLR",
             "n_info_per_stream": N_INFO, "streams_per_step": len(EBN0S), "f": F, "v": V,
-            "radix": radix, "lanes": lanes, "l2": "inputs larger than L2 (192 MiB cycled per step)"}
+            "radix": radix, "lanes": lanes,
+            "path": ("one persistent batched launch per step (vd_batch_plan_launch)" if path == "batch"
+                     else "one vd_decode launch per stream"),
+            "l2": "inputs larger than L2 (192 MiB cycled per step)"}
+
+
+def stream_plan(vd, code, n_streams, radix, lanes, stream):
+    """The six streams as six packets of one batch plan (f=256, v=42)."""
+    tune = vd.VdTune()
+    tune.radix = radix
+    tune.lanes = lanes
+    pk = {"code_id": np.zeros(n_streams, np.int32), "llr_type": np.zeros(n_streams, np.int32),
+          "llr_offset": np.arange(n_streams, dtype=np.int64) * BETA * N_INFO,
+          "n_info": np.full(n_streams, N_INFO, np.int64), "flags": np.zeros(n_streams, np.uint32),
+          "f": np.full(n_streams, F, np.int32), "v": np.full(n_streams, V, np.int32),
+          "out_word_offset": np.arange(n_streams, dtype=np.int64) * (N_INFO // 32)}
+    return vd.BatchPlan([code], pk, tune=tune, stream=stream)
 
 
 def ops_per_bit(f=F, v=V, k=K):
@@ -162,20 +178,32 @@ def run_gpu(args, rank, world):
     for e in EBN0S:
         st = synth.segmented_stream(e)
         streams.append(st.s8().view(np.uint8))
-    llr_dev = [torch.from_numpy(s).to(dev) for s in streams]
     nw = N_INFO // 32
-    outs = [torch.empty(nw, dtype=torch.int32, device=dev) for _ in streams]
-    s = torch.cuda.current_stream(dev)
+    arena = torch.from_numpy(np.concatenate(streams)).to(dev)
+    out_arena = torch.empty(nw * len(streams), dtype=torch.int32, device=dev)
+    llr_dev = [arena[i * BETA * N_INFO:(i + 1) * BETA * N_INFO] for i in range(len(streams))]
+    outs = [out_arena[i * nw:(i + 1) * nw] for i in range(len(streams))]
+    s = torch.cuda.Stream(dev)
     tune = None
     if args.lanes:
         tune = vd.VdTune()
         tune.lanes = args.lanes
     flags = 0
+    plan = stream_plan(vd, code, len(streams), args.radix, args.lanes, s) if args.path == "batch" else None
 
-    def step():
-        for i in range(len(streams)):
+    def one_launch(i):
+        """Launch i of a step: one stream, or the whole batch."""
+        if plan is not None:
+            plan.launch(arena, out_arena, stream=s)
+        else:
             vd.vd_decode(code.handle, llr_dev[i], vd.VD_LLR_S8, N_INFO, F, V, args.radix, flags,
                          outs[i], None, tune, s)
+
+    launches_per_step = 1 if plan is not None else len(streams)
+
+    def step():
+        for i in range(launches_per_step):
+            one_launch(i)
 
     for _ in range(args.warmup):
         step()
@@ -189,7 +217,7 @@ def run_gpu(args, rank, world):
         time.sleep(0.3)
     # per-launch events on the launching stream, for the kernel's own duration
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps * len(streams))]
+          for _ in range(args.steps * launches_per_step)]
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -198,10 +226,9 @@ def run_gpu(args, rank, world):
     t0.record(s)
     k = 0
     for _ in range(args.steps):
-        for i in range(len(streams)):
+        for i in range(launches_per_step):
             ev[k][0].record(s)
-            vd.vd_decode(code.handle, llr_dev[i], vd.VD_LLR_S8, N_INFO, F, V, args.radix, flags,
-                         outs[i], None, tune, s)
+            one_launch(i)
             ev[k][1].record(s)
             k += 1
     t1.record(s)
@@ -229,12 +256,14 @@ def run_gpu(args, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s)
-    for _ in range(e2e_steps):
-        for i in range(len(streams)):
-            llr_dev[i].copy_(host_in[i], non_blocking=True)
-            vd.vd_decode(code.handle, llr_dev[i], vd.VD_LLR_S8, N_INFO, F, V, args.radix, flags,
-                         outs[i], None, tune, s)
-            host_out[i].copy_(outs[i], non_blocking=True)
+    with torch.cuda.stream(s):
+        for _ in range(e2e_steps):
+            for i in range(len(streams)):
+                llr_dev[i].copy_(host_in[i], non_blocking=True)
+            for i in range(launches_per_step):
+                one_launch(i)
+            for i in range(len(streams)):
+                host_out[i].copy_(outs[i], non_blocking=True)
     e1.record(s)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
@@ -248,28 +277,41 @@ def run_gpu(args, rank, world):
     ref_bits = synth.segmented_stream(6.0).bits
     ber6 = float(np.mean(bits != ref_bits))
 
+    if plan is not None:
+        plan.close()
     return {"ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
+            "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "ber_6db": ber6, "n_sm": torch.cuda.get_device_properties(dev).multi_processor_count}
 
 
 def kernel_only(args):
-    """W + K launches of the decode of one 2^24-bit stream (Eb/N0 = 3 dB) and
-    nothing else: the command profilers capture."""
+    """W + K launches and nothing else, for profilers: the batch plan of the six
+    2^24-bit streams (--path batch) or one stream's vd_decode (--path stream)."""
     import torch
     import paper_2011_13579_gb300 as vd
     from paper_2011_13579_gb300 import synth
     code = vd.Code(K, synth.K7_GENS)
-    llr = torch.from_numpy(synth.segmented_stream(3.0).s8().view(np.uint8)).cuda()
-    out = torch.empty(N_INFO // 32, dtype=torch.int32, device="cuda")
-    tune = None
-    if args.lanes:
-        tune = vd.VdTune()
-        tune.lanes = args.lanes
-    for _ in range(args.warmup + args.steps):
-        vd.vd_decode(code.handle, llr, vd.VD_LLR_S8, N_INFO, F, V, args.radix, 0, out, None, tune, None)
-    torch.cuda.synchronize()
+    if args.path == "batch":
+        streams = [synth.segmented_stream(e).s8().view(np.uint8) for e in EBN0S]
+        arena = torch.from_numpy(np.concatenate(streams)).cuda()
+        out = torch.empty(len(streams) * N_INFO // 32, dtype=torch.int32, device="cuda")
+        plan = stream_plan(vd, code, len(streams), args.radix, args.lanes, None)
+        for _ in range(args.warmup + args.steps):
+            plan.launch(arena, out, stream=None)
+        torch.cuda.synchronize()
+        plan.close()
+    else:
+        llr = torch.from_numpy(synth.segmented_stream(3.0).s8().view(np.uint8)).cuda()
+        out = torch.empty(N_INFO // 32, dtype=torch.int32, device="cuda")
+        tune = None
+        if args.lanes:
+            tune = vd.VdTune()
+            tune.lanes = args.lanes
+        for _ in range(args.warmup + args.steps):
+            vd.vd_decode(code.handle, llr, vd.VD_LLR_S8, N_INFO, F, V, args.radix, 0, out, None, tune, None)
+        torch.cuda.synchronize()
     print(json.dumps({"mode": "kernel", "launches": args.warmup + args.steps}))
 
 
@@ -281,6 +323,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--radix", type=int, default=2, choices=[2, 4])
     ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--path", default="batch", choices=["batch", "stream"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
@@ -338,7 +381,7 @@ def main():
     peak_ops = n_sm * 128 * 2 * sm_max_mhz * 1e6
     launch_ms = r["launch_ms"]
     avg_launch_s = statistics.mean(launch_ms) / 1e3
-    ops_per_launch = ops_per_bit() * N_INFO
+    ops_per_launch = ops_per_bit() * r["bits_per_launch"]
     achieved = ops_per_launch / avg_launch_s
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -346,6 +389,7 @@ def main():
         try:
             tr = json.load(open(tr_path))
             if (tr.get("radix") == args.radix and tr.get("lanes", 0) == args.lanes
+                    and tr.get("path", "stream") == args.path
                     and tr.get("source_hash") == kernel_source_hash()):
                 traffic = tr.get("bytes_per_launch")
         except (OSError, ValueError):
@@ -363,14 +407,15 @@ def main():
         "vs_baseline": None,
         "dtype": "u16x2",
         "data": "synthetic",
-        "config": {**workload_config(args.radix, args.lanes), "parallelism": f"replicas{world}"},
+        "config": {**workload_config(args.radix, args.lanes, args.path), "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "vd::stream_kernel", "avg_launch_ms": avg_launch_s * 1e3,
+                     "kernel": "vd::batch_kernel" if args.path == "batch" else "vd::stream_kernel",
+                     "avg_launch_ms": avg_launch_s * 1e3,
                      "ops_per_bit": ops_per_bit(),
                      "peak_basis": f"{n_sm} SMs x 128 lanes x 2 halves x {sm_max_mhz:.0f} MHz"},
         "e2e": r["e2e"],
-        "gpu_launches": args.steps * len(EBN0S),
+        "gpu_launches": args.steps * r["launches_per_step"],
         "clocks": r["clocks"],
         "ber_6db": r["ber_6db"],
     }

@@ -211,6 +211,70 @@ vd_status vd_decode_batch(const vd_code *const *codes, int n_codes, const vd_pac
                           int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena,
                           const vd_tune *tune, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * Continuous batching: packets arriving from many sources are queued on the
+ * host, admitted while the server's device arena has room for their LLRs
+ * and outputs (admission by device memory), and decoded in micro-batches of
+ * everything admitted — one persistent launch per code kind, on a pool of
+ * CUDA streams, so a batch formed while earlier ones are still running
+ * overlaps them on the device.  Frames as in vd_decode: f = 256, v = 42 for
+ * K=7 and f = 512, v = 64 for K=9 unless configured; a packet no longer than
+ * f is one full-length frame.  Each packet's result is the same whether it is
+ * decoded alone or in a mix (the same frames, the same arithmetic).  The
+ * paper has no serving layer.
+ */
+typedef struct vd_server vd_server;
+
+typedef struct vd_server_config {
+    int64_t device_bytes;    /* device arena for admitted packets (default 256 MiB) */
+    int32_t max_batch;       /* packets per micro-batch (default 4096) */
+    int32_t n_streams;       /* CUDA streams that overlap micro-batches (default 3, max 8) */
+    int32_t max_packet_bits; /* largest n_info accepted (default 12000) */
+    int32_t lanes, radix;    /* kernel shape, 0 = defaults */
+    int32_t f7, v7, f9, v9;  /* frame length / overlap per code kind, 0 = defaults */
+    int32_t reserved[5];
+} vd_server_config;
+
+typedef struct vd_completion {
+    uint64_t tag;            /* as given to vd_server_submit */
+    int32_t status;          /* VD_OK, or VD_ECUDA if the device reported an error */
+    int32_t n_words;         /* ceil(n_info/32) decoded words */
+    int64_t word_offset;     /* where they start in the words buffer of vd_server_poll */
+    int64_t submit_ns, admit_ns, done_ns;   /* host steady-clock times: submitted, admitted to
+                                               the device, completion seen by the server */
+} vd_completion;
+
+typedef struct vd_server_stats {
+    int64_t submitted, completed, batches, bits_decoded;
+    int64_t pending;         /* waiting for admission */
+    int64_t arena_used;      /* bytes of the device arena in use */
+    int64_t error;           /* last CUDA error seen by the worker (0 = none) */
+} vd_server_stats;
+
+/* Creates a server (allocates its arena, pinned mirror and per-stream buffers,
+ * and starts its worker thread) on the current device. */
+vd_status vd_server_create(vd_server **out, const vd_code *const *codes, int n_codes,
+                           const vd_server_config *cfg);
+
+/* Queues one packet: n_values received values (int8, or 4-bit two per byte) in
+ * host memory, copied before returning; n_info information bits; flags as
+ * vd_decode.  Never blocks on the device. */
+vd_status vd_server_submit(vd_server *server, int code_id, int llr_type, const void *host_llr,
+                           int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag);
+
+/* Moves up to max_completions finished packets out: their records into comp
+ * and their decoded words into words (capacity words_cap).  Returns the
+ * number of records written (0 if none is ready). */
+int64_t vd_server_poll(vd_server *server, vd_completion *comp, int64_t max_completions,
+                       uint32_t *words, int64_t words_cap);
+
+/* Counters of the server. */
+vd_status vd_server_stats_get(vd_server *server, vd_server_stats *out);
+
+/* Stops the worker, waits for the device, frees everything. */
+void vd_server_destroy(vd_server *server);
+
 /*
  * Waits for the stream, then reads and clears the library's device status
  * word.  VD_EBOUNDS if a kernel refused work that would have overrun its

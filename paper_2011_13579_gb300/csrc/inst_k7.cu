@@ -1,5 +1,6 @@
 // Kernel instantiations for the K=7 code (generators 171/133).
 #include "vd_launch.h"
+#include "vd_stream_f32.cuh"
 
 namespace vd {
 
@@ -88,6 +89,20 @@ bool geom_k7(int lanes, bool radix4, KernelGeom *g) {
         g->U = radix4 ? StreamCfg<7, 2, GENS_K7, 4, true>::U : StreamCfg<7, 2, GENS_K7, 4, false>::U;
         g->NW = radix4 ? StreamCfg<7, 2, GENS_K7, 4, true>::NW : StreamCfg<7, 2, GENS_K7, 4, false>::NW;
         return true;
+    default: return false;
+    }
+}
+
+cudaError_t launch_stream_f32_k7(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st) {
+    switch (lanes) {
+    case 2: stream_kernel_f32<7, 2, GENS_K7, 2, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(p); return cudaGetLastError();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool geom_f32_k7(int lanes, KernelGeom *g) {
+    switch (lanes) {
+    case 2: g->U = StreamCfgF32<7, 2, GENS_K7, 2>::U; g->NW = StreamCfgF32<7, 2, GENS_K7, 2>::NW; return true;
     default: return false;
     }
 }

@@ -1,5 +1,6 @@
 // Kernel instantiations for the K=9 code (generators 557/663/711).
 #include "vd_launch.h"
+#include "vd_stream_f32.cuh"
 
 namespace vd {
 
@@ -78,6 +79,20 @@ bool geom_k9(int lanes, bool radix4, KernelGeom *g) {
         g->U = radix4 ? StreamCfg<9, 3, GENS_K9, 8, true>::U : StreamCfg<9, 3, GENS_K9, 8, false>::U;
         g->NW = radix4 ? StreamCfg<9, 3, GENS_K9, 8, true>::NW : StreamCfg<9, 3, GENS_K9, 8, false>::NW;
         return true;
+    default: return false;
+    }
+}
+
+cudaError_t launch_stream_f32_k9(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st) {
+    switch (lanes) {
+    case 8: stream_kernel_f32<9, 3, GENS_K9, 8, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(p); return cudaGetLastError();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool geom_f32_k9(int lanes, KernelGeom *g) {
+    switch (lanes) {
+    case 8: g->U = StreamCfgF32<9, 3, GENS_K9, 8>::U; g->NW = StreamCfgF32<9, 3, GENS_K9, 8>::NW; return true;
     default: return false;
     }
 }

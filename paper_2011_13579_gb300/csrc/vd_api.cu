@@ -306,14 +306,19 @@ struct Plan {
 };
 
 vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, uint32_t flags,
-                    const vd_tune *tune, Plan *pl) {
-    pl->r4 = radix == 4;
+                    const vd_tune *tune, Plan *pl, bool f32 = false) {
+    pl->r4 = radix == 4 && !f32;
     if (tune && tune->lanes > 0) {
         pl->lanes = tune->lanes;
+    } else if (f32) {
+        pl->lanes = c->kind == vd::KIND_K7_R2 ? 2 : 8;
     } else if (!default_lanes(c->kind, &pl->lanes)) {
         return fail(VD_EUNSUPPORTED, "no kernel for this code");
     }
-    if (!geometry(c->kind, pl->lanes, pl->r4, &pl->geom))
+    const bool have = f32 ? (c->kind == vd::KIND_K7_R2 ? vd::geom_f32_k7(pl->lanes, &pl->geom)
+                                                       : vd::geom_f32_k9(pl->lanes, &pl->geom))
+                          : geometry(c->kind, pl->lanes, pl->r4, &pl->geom);
+    if (!have)
         return fail(VD_EUNSUPPORTED, "no kernel with %d lanes per frame pair (radix %d) for K=%d",
                     pl->lanes, radix, c->K);
     pl->T = n_info + ((flags & VD_TERMINATED) ? c->K - 1 : 0);
@@ -365,14 +370,16 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     vd_status st = check_decode_args(c, d_llr, llr_type, n_info, f, v, radix, flags, d_out);
     if (st != VD_OK) return st;
     if (n_info == 0) return VD_OK;
-    if (llr_type == VD_LLR_F16) return fail(VD_EUNSUPPORTED, "fp16 LLRs are not built yet");
+    const bool f32 = llr_type == VD_LLR_F16;
+    if (f32 && c->punctured) return fail(VD_EUNSUPPORTED, "fp16 LLRs of punctured codes are not supported");
+    if (f32 && d_pm) return fail(VD_EUNSUPPORTED, "metric output is for integer LLRs only");
     cudaStream_t cs = (cudaStream_t)stream;
     Plan pl;
-    st = make_plan(c, n_info, f, v, radix, flags, tune, &pl);
+    st = make_plan(c, n_info, f, v, radix, flags, tune, &pl, f32);
     if (st != VD_OK) return st;
 
     const int8_t *llr = (const int8_t *)d_llr;
-    if (c->punctured || llr_type == VD_LLR_S4) {
+    if (!f32 && (c->punctured || llr_type == VD_LLR_S4)) {
         void *buf = nullptr;
         st = get_scratch(1, (size_t)pl.T * c->beta, cs, &buf);
         if (st != VD_OK) return st;
@@ -419,9 +426,16 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     p.status = status;
     if (pl.blocks > 0x7FFFFFFF) return fail(VD_EINVAL, "stream too long for one launch");
     cudaError_t e;
+    p.llr_bytes = pl.T * c->beta * (f32 ? 2 : 1);
     switch (c->kind) {
-    case vd::KIND_K7_R2: e = vd::launch_stream_k7(pl.lanes, pl.r4, p, pl.blocks, cs); break;
-    case vd::KIND_K9_R3: e = vd::launch_stream_k9(pl.lanes, pl.r4, p, pl.blocks, cs); break;
+    case vd::KIND_K7_R2:
+        e = f32 ? vd::launch_stream_f32_k7(pl.lanes, p, pl.blocks, cs)
+                : vd::launch_stream_k7(pl.lanes, pl.r4, p, pl.blocks, cs);
+        break;
+    case vd::KIND_K9_R3:
+        e = f32 ? vd::launch_stream_f32_k9(pl.lanes, p, pl.blocks, cs)
+                : vd::launch_stream_k9(pl.lanes, pl.r4, p, pl.blocks, cs);
+        break;
     default: return fail(VD_EUNSUPPORTED, "no kernel for this code");
     }
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");

@@ -33,31 +33,10 @@ vd_status cuda_fail(cudaError_t e, const char *what) {
     return fail(VD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-constexpr int kMaxBatchCodes = 16;
-
-// ------------------------------------------------------------- pre-pass
-
-struct PrepCode {
-    int beta, period, kept_per_period, pad;
-    uint8_t punct[4][8];
-    int kept_prefix[9];
-};
-
-struct PrepJob {
-    int64_t src_off;     // first kept value of the packet in the caller's arena (values)
-    int64_t dst_off;     // byte offset of the packet's [T][beta] int8 in the internal arena
-    int64_t T;
-    int32_t code_slot;
-    int32_t llr_type;
-};
-
-struct PrepBatchParams {
-    const uint8_t *src;
-    int8_t *dst;
-    const PrepJob *jobs;
-    int64_t n_jobs;
-    PrepCode codes[kMaxBatchCodes];
-};
+using vd::kMaxBatchCodes;
+using vd::PrepBatchParams;
+using vd::PrepCode;
+using vd::PrepJob;
 
 __device__ __forceinline__ int8_t batch_kept_value(const uint8_t *src, int64_t k, int llr_type) {
     if (llr_type == VD_LLR_S4) {
@@ -524,3 +503,21 @@ extern "C" vd_status vd_decode_batch(const vd_code *const *codes, int n_codes, c
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return VD_OK;
 }
+
+namespace vd {
+
+cudaError_t launch_prep_batch(const PrepBatchParams &p, cudaStream_t st) {
+    if (p.n_jobs <= 0) return cudaSuccess;
+    prep_batch_kernel<<<(unsigned)p.n_jobs, 128, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+void fill_prep_code(const vd_code *c, PrepCode *pc) {
+    pc->beta = c->beta;
+    pc->period = c->period;
+    pc->kept_per_period = c->kept_per_period;
+    memcpy(pc->punct, c->punct, sizeof pc->punct);
+    memcpy(pc->kept_prefix, c->kept_prefix, sizeof pc->kept_prefix);
+}
+
+}  // namespace vd

@@ -54,7 +54,7 @@ __device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t
 }
 
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
-__global__ void __launch_bounds__(NT, 3) batch_kernel(const BatchParams p) {
+__global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const BatchParams p) {
     constexpr int PPW = 32 / L;
     constexpr int NW = StreamCfg<K, BETA, GENS, L, RADIX4>::NW;
     const int wlane = (int)(threadIdx.x & 31u);

@@ -1,6 +1,8 @@
 // Internal definition of the opaque vd_code object (shared by the C-ABI sources).
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
+
 #include "vd_launch.h"
 
 struct vd_code {
@@ -16,3 +18,36 @@ struct vd_code {
 
 // Sets the calling thread's message returned by vd_last_error().
 void vd_internal_set_error(const char *msg);
+
+namespace vd {
+
+// Input pre-pass shared by batches and the server: expands the transmitted
+// values of each listed packet to int8 [T][beta] (0 at erased positions).
+constexpr int kMaxBatchCodes = 16;
+
+struct PrepCode {
+    int beta, period, kept_per_period, pad;
+    uint8_t punct[4][8];
+    int kept_prefix[9];
+};
+
+struct PrepJob {
+    int64_t src_off;     // first kept value of the packet in the source arena (values)
+    int64_t dst_off;     // byte offset of the packet's [T][beta] int8 in the destination
+    int64_t T;
+    int32_t code_slot;
+    int32_t llr_type;
+};
+
+struct PrepBatchParams {
+    const uint8_t *src;
+    int8_t *dst;
+    const PrepJob *jobs;
+    int64_t n_jobs;
+    PrepCode codes[kMaxBatchCodes];
+};
+
+cudaError_t launch_prep_batch(const PrepBatchParams &p, cudaStream_t st);
+void fill_prep_code(const vd_code *c, PrepCode *pc);
+
+}  // namespace vd

@@ -34,6 +34,10 @@ cudaError_t launch_batch_k9(int lanes, bool radix4, const BatchParams &p, int64_
                             cudaStream_t st);
 cudaError_t batch_occupancy_k7(int lanes, bool radix4, int *blocks_per_sm);
 cudaError_t batch_occupancy_k9(int lanes, bool radix4, int *blocks_per_sm);
+cudaError_t launch_stream_f32_k7(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st);
+cudaError_t launch_stream_f32_k9(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st);
+bool geom_f32_k7(int lanes, KernelGeom *g);
+bool geom_f32_k9(int lanes, KernelGeom *g);
 bool geom_k7(int lanes, bool radix4, KernelGeom *g);
 bool geom_k9(int lanes, bool radix4, KernelGeom *g);
 
