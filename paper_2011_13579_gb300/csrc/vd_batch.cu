@@ -342,7 +342,8 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
         g.wpad_cap = frs.empty() ? U : (int32_t)frs.front().wpad;
         const int64_t tasks_blocks = (g.n_tasks * 32 + vd::kThreads - 1) / vd::kThreads;
         g.blocks = std::max<int64_t>(1, std::min(g.blocks, tasks_blocks));
-        g.surv_bytes = (size_t)g.blocks * vd::kThreads * (size_t)g.wpad_cap * g.geom.NW * 4u;
+        // two survivor buffers per resident warp: one being written, one being traced back
+        g.surv_bytes = 2u * (size_t)g.blocks * vd::kThreads * (size_t)g.wpad_cap * g.geom.NW * 4u;
         if ((st = upload(&g.d_pk, pds, cs)) != VD_OK || (st = upload(&g.d_pairs, pairs, cs)) != VD_OK) {
             pl->groups.push_back(g);
             free_plan(pl);

@@ -2,7 +2,7 @@
 // one launch.  The host sorts every frame of every packet by length, pairs
 // neighbours, and groups 32/L pairs into a warp task; resident warps pull
 // tasks from a global counter (longest first) and run the same frame-pair
-// decoder as the stream kernel (decode_pair) on each.
+// forward procedure and traceback as the stream kernel on each.
 #pragma once
 #include "vd_stream.cuh"
 
@@ -33,7 +33,7 @@ struct BatchParams {
     const int8_t *llr_int;    // the internal arena (depunctured / unpacked packets)
     uint32_t *out;            // the caller's output arena
     int *counter;             // task counter, zero at launch
-    uint32_t *surv;           // per resident warp: wpad_cap x 32 x NW words
+    uint32_t *surv;           // per resident warp: 2 x wpad_cap x 32 x NW words
     int32_t wpad_cap;
     int *status;
 };
@@ -53,17 +53,31 @@ __device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t
     return frame_task(llr, p.out + d.out_word_off, nullptr, (int64_t)s, n_win, d.n_info, T, d.f, d.v, fl);
 }
 
+// Each resident warp loops over tasks.  While it runs the forward procedure of
+// a task, it walks the previous task's traceback one group per chunk (the two
+// tasks' survivors live in the two halves of the warp's scratch), so the
+// traceback's latency hides behind forward work.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
 __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const BatchParams p) {
     constexpr int PPW = 32 / L;
-    constexpr int NW = StreamCfg<K, BETA, GENS, L, RADIX4>::NW;
+    using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
+    constexpr int NW = Cfg::NW;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW>;
+    __shared__ TbState tbs[NT];
+    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int wlane = (int)(threadIdx.x & 31u);
     const int group = wlane / L;
     const int lane = wlane % L;
     const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
     const int grp_base = wlane & ~(L - 1);
     const int64_t gwarp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    uint32_t *surv = p.surv + (size_t)gwarp * (size_t)p.wpad_cap * 32u * (size_t)NW;
+    const size_t buf_words = (size_t)p.wpad_cap * 32u * (size_t)NW;
+    uint32_t *surv = p.surv + (size_t)gwarp * 2u * buf_words;
+    uint32_t *my_stg = stg[threadIdx.x >> 5];
+    TbState &pend = tbs[threadIdx.x];
+    pend.t0 = -1;
+    pend.tau_store = 0;
+    int buf = 0;
     while (true) {
         int t = 0;
         if (wlane == 0) t = atomicAdd(p.counter, 1);
@@ -79,9 +93,17 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
             ft[0] = packet_frame<K>(p, 0xFFFFFFFFu, 0);
             ft[1] = ft[0];
         }
-        decode_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_cap, wlane, lane, gmask, grp_base, p.status);
-        __syncwarp();   // the next task reuses this warp's scratch
+        TbState tb;
+        forward_pair<K, BETA, GENS, L, RADIX4>(
+            ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, tb,
+            [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+        Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+        pend = tb;
+        if (Tb::active(pend)) Tb::begin(pend, my_stg, wlane);
+        buf ^= 1;
+        __syncwarp();
     }
+    Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
 }
 
 }  // namespace vd

@@ -459,7 +459,7 @@ extern "C" vd_status vd_server_create(vd_server **out, const vd_code *const *cod
             kr.blocks = (int64_t)s->n_sm * bps;
             const int64_t wmax = (int64_t)kr.f + std::max(2 * kr.v, kr.K - 1);
             kr.wpad_cap = (int32_t)(((wmax + kr.geom.U - 1) / kr.geom.U) * kr.geom.U);
-            const size_t surv = (size_t)kr.blocks * vd::kThreads * (size_t)kr.wpad_cap * kr.geom.NW * 4u;
+            const size_t surv = 2u * (size_t)kr.blocks * vd::kThreads * (size_t)kr.wpad_cap * kr.geom.NW * 4u;
             if (cudaMalloc((void **)&kr.d_pk, (size_t)c.max_batch * sizeof(vd::PacketDesc)) != cudaSuccess ||
                 cudaMalloc((void **)&kr.d_pairs, (size_t)max_frames * sizeof(vd::PairRef)) != cudaSuccess ||
                 cudaMalloc((void **)&kr.d_surv, surv) != cudaSuccess ||

@@ -189,148 +189,214 @@ __host__ __device__ constexpr uint32_t bitk_mask(int k) {
          : k == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
-// Backward procedure (Algorithm 2) for one pair of frames, from the final
-// registers R[h] (frame h's traceback start, in register space) down to each
-// frame's first decoded stage.  Every lane of the group follows both frames;
-// the lane that owns the current register supplies the decision bit (one
-// shuffle).  Stages are walked in groups of K-1 starting at Wpad-1, so the
-// phase of every stage in a group is a compile-time constant; the next
-// group's survivor words are loaded while the current group is walked.
+// ------------------------------------------------------------ traceback
+//
+// Backward procedure (Algorithm 2) for one pair of frames, resumable: it walks
+// groups of K-1 stages (so the phase of every stage in a group is a
+// compile-time constant) from Wpad-1 down to the frames' first decoded
+// stages.  A persistent warp calls step() once per chunk of the NEXT frame
+// pair's forward pass, so the traceback's dependent chain and its memory
+// latency hide behind forward work.  The survivor words of the next two
+// groups are copied into a per-warp shared-memory staging area by cp.async
+// while earlier groups are walked; the per-lane state lives in shared memory
+// between steps.  Every lane of a group follows both frames; the lane that
+// owns the current register supplies its decision bit (one shuffle).
 // Survivor words: bit (r & 31) of word (r >> 5) holds register r of the lane
 // (r & 15 at bit 16h when a lane has 16 registers or fewer), frame 0 first.
+
+struct TbState {
+    uint32_t *out[2];        // packed output of each frame's stream
+    const uint32_t *surv;    // this lane's survivor words (stage stride 32 * NW words)
+    uint32_t R[2];           // current register of each frame (traceback state)
+    uint32_t oacc[2];        // output bits being assembled
+    int32_t t0;              // first stage of the next group; finished when t0 < tau_store
+    int32_t tau_store;
+    int32_t tauo[2], taue[2];
+    int32_t toff[2];         // stage in the frame's stream = tau + toff
+    int32_t slot;            // staging slot holding group t0
+    int32_t pad;
+};
+
+__device__ __forceinline__ void cp_async_bytes16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes8(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes4(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int K, int L, bool RADIX4, int NR, int NW>
-__device__ __forceinline__ void traceback_pair(const FrameTask (&ft)[2], const uint32_t *surv,
-                                               uint32_t (&R)[2], const int (&tauo)[2],
-                                               const int (&taue)[2], const int64_t (&toff)[2],
-                                               int tau_store, int Wpad, int wlane, int lane,
-                                               unsigned gmask, int grp_base) {
-    constexpr int NB = K - 1;
-    constexpr int LR = ilog2(NR);
-    constexpr int WPF = NR >= 32 ? NR / 32 : 1;
-    constexpr int G = NB;
-    uint32_t oacc[2] = {0u, 0u};
-    const uint32_t *my = surv + (size_t)wlane * NW;
+struct Traceback {
+    static constexpr int NB = K - 1;
+    static constexpr int G = NB;                 // stages per group
+    static constexpr int LR = ilog2(NR);
+    static constexpr int WPF = NR >= 32 ? NR / 32 : 1;
+    static constexpr int SLOT_WORDS = G * 32 * NW;
+    static constexpr int STAGE_WORDS = 2 * SLOT_WORDS;   // per warp
 
-    auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
-        // bit of register Rh of frame h in this lane's words for one stage
-        uint32_t word, bit;
-        if constexpr (NR >= 32) {
-            word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
-            bit = Rh & 31u;
-        } else {
-            word = wd[0];
-            bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
-        }
-        return (word >> bit) & 1u;
-    };
-    auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
-        if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
-        else return bits;
-    };
-    auto emit = [&](int h, int t, uint32_t u) {
-        if (t < taue[h]) {
-            oacc[h] = (oacc[h] << 1) | u;
-            const int64_t tabs = (int64_t)t + toff[h];
-            if ((tabs & 31) == 0) {
-                if (lane == (L > 1 ? h : 0)) ft[h].out[tabs >> 5] = oacc[h];
-                oacc[h] = 0;
-            }
-        }
-    };
-
-    uint32_t bufA[G][NW], bufB[G][NW];
-    auto load_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+    // Copies the words of stages t0, t0-1, .., t0-G+1 (those >= tau_store) to a slot.
+    __device__ static void issue(const TbState &s, int t0, uint32_t *slot, int wlane) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int t = t0 - g;
-            const uint32_t *src = my + (size_t)t * 32 * NW;
-            if (t >= tau_store) {
+            if (t >= s.tau_store) {
+                uint32_t *dst = slot + (g * 32 + wlane) * NW;
+                const uint32_t *src = s.surv + (size_t)t * 32 * NW;
                 if constexpr (NW == 1) {
-                    buf[g][0] = __ldg(src);
+                    cp_async_bytes4(dst, src);
                 } else if constexpr (NW == 2) {
-                    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(src));
-                    buf[g][0] = x.x; buf[g][1] = x.y;
+                    cp_async_bytes8(dst, src);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < NW; i += 4) {
-                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + i));
-                        buf[g][i] = x.x; buf[g][i + 1] = x.y; buf[g][i + 2] = x.z; buf[g][i + 3] = x.w;
-                    }
+                    for (int i = 0; i < NW; i += 4) cp_async_bytes16(dst + i, src + i);
                 }
-            } else {
-#pragma unroll
-                for (int i = 0; i < NW; ++i) buf[g][i] = 0u;
             }
         }
-    };
-    auto walk_group = [&](int t0, uint32_t (&buf)[G][NW]) {
+        cp_async_commit();
+    }
+
+    __device__ static bool active(const TbState &s) { return s.t0 >= s.tau_store; }
+
+    // Starts the copies of the first two groups.
+    __device__ static void begin(TbState &s, uint32_t *stg, int wlane) {
+        s.slot = 0;
+        issue(s, s.t0, stg, wlane);
+        issue(s, s.t0 - G, stg + SLOT_WORDS, wlane);
+    }
+
+    // Walks one group (if any remains) and refills its slot with the group two ahead.
+    __device__ static void step(TbState &s, uint32_t *stg, int wlane, int lane, unsigned gmask,
+                                int grp_base) {
+        if (!active(s)) return;
+        cp_async_wait<1>();
+        const uint32_t *slot = stg + s.slot * SLOT_WORDS;
+        const int t0 = s.t0;
+        uint32_t R0 = s.R[0], R1 = s.R[1], o0 = s.oacc[0], o1 = s.oacc[1];
+        const int tauo0 = s.tauo[0], tauo1 = s.tauo[1], taue0 = s.taue[0], taue1 = s.taue[1];
+        auto words = [&](int g, uint32_t (&wd)[NW]) {
+            const uint32_t *p = slot + (g * 32 + wlane) * NW;
+            if constexpr (NW == 1) {
+                wd[0] = p[0];
+            } else if constexpr (NW == 2) {
+                const uint2 x = *reinterpret_cast<const uint2 *>(p);
+                wd[0] = x.x; wd[1] = x.y;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; i += 4) {
+                    const uint4 x = *reinterpret_cast<const uint4 *>(p + i);
+                    wd[i] = x.x; wd[i + 1] = x.y; wd[i + 2] = x.z; wd[i + 3] = x.w;
+                }
+            }
+        };
+        auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
+            uint32_t word, bit;
+            if constexpr (NR >= 32) {
+                word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
+                bit = Rh & 31u;
+            } else {
+                word = wd[0];
+                bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
+            }
+            return (word >> bit) & 1u;
+        };
+        auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
+            if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
+            else return bits;
+        };
+        auto emit = [&](int h, int t, uint32_t u) {
+            uint32_t &o = h ? o1 : o0;
+            if (t < (h ? taue1 : taue0)) {
+                o = (o << 1) | u;
+                const int tabs = t + s.toff[h];
+                if ((tabs & 31) == 0) {
+                    if (lane == (L > 1 ? h : 0)) s.out[h][tabs >> 5] = o;
+                    o = 0;
+                }
+            }
+        };
         if constexpr (!RADIX4) {
             static_for<G>([&](auto gc) {
                 constexpr int g = decltype(gc)::value;
-                constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // t0 = -1 mod (K-1)
+                constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // group starts at -1 mod (K-1)
                 const int t = t0 - g;
+                uint32_t wd[NW];
+                words(g, wd);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (t >= tauo[h]) {
-                        const uint32_t d = owner_bits(decision(buf[g], h, R[h]), R[h]);
-                        const uint32_t u = (R[h] >> ph) & 1u;
-                        R[h] = (R[h] & ~(1u << ph)) | (d << ph);
+                    uint32_t &Rh = h ? R1 : R0;
+                    if (t >= (h ? tauo1 : tauo0)) {
+                        const uint32_t d = owner_bits(decision(wd, h, Rh), Rh);
+                        const uint32_t u = (Rh >> ph) & 1u;
+                        Rh = (Rh & ~(1u << ph)) | (d << ph);
                         emit(h, t, u);
                     }
                 }
             });
         } else {
-            // pairs (t, t-1): t is the second stage of a pair (odd offset in a chunk)
+            // pairs (t, t-1): t is the second stage of a pair
             static_for<G / 2>([&](auto gc) {
                 constexpr int g = 2 * decltype(gc)::value;
                 constexpr int ph2 = ((NB - 1 - g) % NB + NB) % NB;
                 constexpr int ph1 = ((NB - 2 - g) % NB + NB) % NB;
                 const int t = t0 - g;
+                uint32_t w2[NW], w1[NW];
+                words(g, w2);
+                words(g + 1, w1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (t >= tauo[h]) {
-                        const uint32_t b2 = decision(buf[g], h, R[h]);
-                        const uint32_t b1 = decision(buf[g + 1], h, R[h]);   // same position
-                        const uint32_t bb = owner_bits(b2 | (b1 << 1), R[h]);
-                        const uint32_t u2 = (R[h] >> ph2) & 1u;
-                        const uint32_t m = (R[h] & ~(1u << ph2)) | ((bb & 1u) << ph2);
+                    uint32_t &Rh = h ? R1 : R0;
+                    if (t >= (h ? tauo1 : tauo0)) {
+                        const uint32_t b2 = decision(w2, h, Rh);
+                        const uint32_t b1 = decision(w1, h, Rh);   // same position
+                        const uint32_t bb = owner_bits(b2 | (b1 << 1), Rh);
+                        const uint32_t u2 = (Rh >> ph2) & 1u;
+                        const uint32_t m = (Rh & ~(1u << ph2)) | ((bb & 1u) << ph2);
                         emit(h, t, u2);
-                        if (t - 1 >= tauo[h]) {
+                        if (t - 1 >= (h ? tauo1 : tauo0)) {
                             const uint32_t u1 = (m >> ph1) & 1u;
-                            R[h] = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
+                            Rh = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
                             emit(h, t - 1, u1);
                         } else {
-                            R[h] = m;
+                            Rh = m;
                         }
                     }
                 }
             });
         }
-    };
-
-    int t0 = Wpad - 1;
-    if (t0 >= tau_store) {
-        load_group(t0, bufA);
-        while (true) {
-            if (t0 - G >= tau_store) load_group(t0 - G, bufB);
-            walk_group(t0, bufA);
-            t0 -= G;
-            if (t0 < tau_store) break;
-            if (t0 - G >= tau_store) load_group(t0 - G, bufA);
-            walk_group(t0, bufB);
-            t0 -= G;
-            if (t0 < tau_store) break;
-        }
+        s.R[0] = R0; s.R[1] = R1; s.oacc[0] = o0; s.oacc[1] = o1;
+        // refill the consumed slot with the group two ahead, then advance
+        issue(s, t0 - 2 * G, stg + s.slot * SLOT_WORDS, wlane);
+        s.t0 = t0 - G;
+        s.slot ^= 1;
     }
-}
 
-// Forward procedure, survivor storage and traceback for one pair of frames.
-// Called by one group of L lanes; surv is this warp's scratch (wpad_cap
-// stages x 32 lanes x NW words); wlane is the lane in the warp.
-template <int K, int BETA, uint64_t GENS, int L, bool RADIX4>
-__device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *surv, int wpad_cap,
-                                            int wlane, int lane, unsigned gmask, int grp_base,
-                                            int *status) {
+    // Walks every remaining group and waits for all copies.
+    __device__ static void drain(TbState &s, uint32_t *stg, int wlane, int lane, unsigned gmask,
+                                 int grp_base) {
+        while (active(s)) step(s, stg, wlane, lane, gmask, grp_base);
+        cp_async_wait<0>();
+    }
+};
+
+// Forward procedure (Algorithm 1) and survivor storage for one pair of frames.
+// Called by one group of L lanes; surv is the frame pair's survivor buffer in
+// this warp's scratch (wpad_cap stages x 32 lanes x NW words); wlane is the
+// lane in the warp.  hook() runs after every chunk of U stages (the
+// persistent kernel walks a previous pair's traceback there).  On return tb
+// holds the traceback start of this pair; returns false (tb inactive) if the
+// pair does not fit the scratch, which host plans never produce.
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, typename Hook>
+__device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t *surv, int wpad_cap,
+                                             int wlane, int lane, unsigned gmask, int grp_base,
+                                             int *status, TbState &tb, Hook &&hook) {
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     using C = typename Cfg::C;
     constexpr int NB = Cfg::NB, NR = Cfg::NR, LR = Cfg::LR, U = Cfg::U, UW = Cfg::UW;
@@ -354,9 +420,11 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
     }
     const int64_t Wmax = W[0] > W[1] ? W[0] : W[1];
     const int Wpad = (int)(((Wmax + U - 1) / U) * U);
+    tb.t0 = -1;
+    tb.tau_store = 0;
     if (Wpad > wpad_cap) {   // never happens for plans built by the host; refuse, do not overrun
         if (lane == 0) atomicOr(status, 1);
-        return;
+        return false;
     }
     int tau0[2], tauo[2], taue[2];
 #pragma unroll
@@ -646,6 +714,7 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
 #pragma unroll
             for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
         }
+        hook();
     }
 
     // ------------------------------------------------- traceback start state
@@ -699,15 +768,31 @@ __device__ __forceinline__ void decode_pair(const FrameTask (&ft)[2], uint32_t *
         }
     }
 
-    const int64_t toff[2] = {fa[0] - tau0[0], fa[1] - tau0[1]};
-    traceback_pair<K, L, RADIX4, NR, NW>(ft, surv, R, tauo, taue, toff, tau_store, Wpad, wlane, lane,
-                                         gmask, grp_base);
+    tb.out[0] = ft[0].out;
+    tb.out[1] = ft[1].out;
+    tb.surv = surv + (size_t)wlane * NW;
+    tb.R[0] = R[0];
+    tb.R[1] = R[1];
+    tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.t0 = Wpad - 1;
+    tb.tau_store = tau_store;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        tb.tauo[h] = tauo[h];
+        tb.taue[h] = taue[h];
+        tb.toff[h] = (int32_t)(fa[h] - tau0[h]);
+    }
+    return true;
 }
 
 // Segmented decode of one stream: frame pair q = (2q, 2q+1) per group of L lanes.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
 __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     constexpr int NS = 1 << (K - 1);
+    using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW>;
+    __shared__ TbState tbs[NT];
+    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
     const int64_t q = gtid / L;
     const int lane = (int)(gtid % L);
@@ -722,9 +807,17 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
         ft[h] = frame_task(p.llr, p.out, p.pm_out ? p.pm_out + s * NS : nullptr, s, p.n_win,
                            p.n_info, p.T, p.f, p.v, p.flags);
     }
-    uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u *
-                                  (size_t)StreamCfg<K, BETA, GENS, L, RADIX4>::NW;
-    decode_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status);
+    uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::NW;
+    TbState tb;
+    forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
+                                           tb, [] {});
+    TbState &st = tbs[threadIdx.x];
+    st = tb;
+    uint32_t *my_stg = stg[threadIdx.x >> 5];
+    if (Tb::active(st)) {
+        Tb::begin(st, my_stg, wlane);
+        Tb::drain(st, my_stg, wlane, lane, gmask, grp_base);
+    }
 }
 
 }  // namespace vd

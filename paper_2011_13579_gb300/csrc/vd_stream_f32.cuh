@@ -37,9 +37,9 @@ __device__ __forceinline__ float half_at(uint32_t word, int hi) {
 }
 
 template <int K, int BETA, uint64_t GENS, int L>
-__device__ __forceinline__ void decode_pair_f32(const FrameTask (&ft)[2], uint32_t *surv, int wpad_cap,
-                                                int wlane, int lane, unsigned gmask, int grp_base,
-                                                int *status) {
+__device__ __forceinline__ bool forward_pair_f32(const FrameTask (&ft)[2], uint32_t *surv, int wpad_cap,
+                                                 int wlane, int lane, unsigned gmask, int grp_base,
+                                                 int *status, TbState &tb) {
     using Cfg = StreamCfgF32<K, BETA, GENS, L>;
     using C = typename Cfg::C;
     constexpr int NB = Cfg::NB, NR = Cfg::NR, LR = Cfg::LR, U = Cfg::U, UW = Cfg::UW, NW = Cfg::NW;
@@ -60,9 +60,11 @@ __device__ __forceinline__ void decode_pair_f32(const FrameTask (&ft)[2], uint32
     }
     const int64_t Wmax = W[0] > W[1] ? W[0] : W[1];
     const int Wpad = (int)(((Wmax + U - 1) / U) * U);
+    tb.t0 = -1;
+    tb.tau_store = 0;
     if (Wpad > wpad_cap) {
         if (lane == 0) atomicOr(status, 1);
-        return;
+        return false;
     }
     int tau0[2], tauo[2], taue[2];
 #pragma unroll
@@ -245,13 +247,29 @@ __device__ __forceinline__ void decode_pair_f32(const FrameTask (&ft)[2], uint32
         }
         R[h] = term[h] ? 0u : bR;
     }
-    const int64_t toff[2] = {fa[0] - tau0[0], fa[1] - tau0[1]};
-    traceback_pair<K, L, false, NR, NW>(ft, surv, R, tauo, taue, toff, tau_store, Wpad, wlane, lane,
-                                        gmask, grp_base);
+    tb.out[0] = ft[0].out;
+    tb.out[1] = ft[1].out;
+    tb.surv = surv + (size_t)wlane * NW;
+    tb.R[0] = R[0];
+    tb.R[1] = R[1];
+    tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.t0 = Wpad - 1;
+    tb.tau_store = tau_store;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        tb.tauo[h] = tauo[h];
+        tb.taue[h] = taue[h];
+        tb.toff[h] = (int32_t)(fa[h] - tau0[h]);
+    }
+    return true;
 }
 
 template <int K, int BETA, uint64_t GENS, int L, int NT>
 __global__ void __launch_bounds__(NT) stream_kernel_f32(const StreamParams p) {
+    using Cfg = StreamCfgF32<K, BETA, GENS, L>;
+    using Tb = Traceback<K, L, false, Cfg::NR, Cfg::NW>;
+    __shared__ TbState tbs[NT];
+    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
     const int64_t q = gtid / L;
     const int lane = (int)(gtid % L);
@@ -267,7 +285,15 @@ __global__ void __launch_bounds__(NT) stream_kernel_f32(const StreamParams p) {
     }
     uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u *
                                   (size_t)StreamCfgF32<K, BETA, GENS, L>::NW;
-    decode_pair_f32<K, BETA, GENS, L>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status);
+    TbState tb;
+    forward_pair_f32<K, BETA, GENS, L>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status, tb);
+    TbState &st = tbs[threadIdx.x];
+    st = tb;
+    uint32_t *my_stg = stg[threadIdx.x >> 5];
+    if (Tb::active(st)) {
+        Tb::begin(st, my_stg, wlane);
+        Tb::drain(st, my_stg, wlane, lane, gmask, grp_base);
+    }
 }
 
 }  // namespace vd
