@@ -23,7 +23,9 @@ __all__ = [
     "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
     "vd_decode", "vd_decode_batch", "vd_batch_plan_create", "vd_batch_plan_launch",
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
-    "VdPacket", "VdBatchInfo", "BatchPlan", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
+    "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
+    "vd_server_destroy", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -60,6 +62,26 @@ class VdBatchInfo(ctypes.Structure):
                 ("resident_warps", ctypes.c_int64), ("lanes", ctypes.c_int32),
                 ("radix", ctypes.c_int32), ("n_launches", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class VdServerConfig(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("max_packet_bits", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("radix", ctypes.c_int32), ("f7", ctypes.c_int32),
+                ("v7", ctypes.c_int32), ("f9", ctypes.c_int32), ("v9", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class VdCompletion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_words", ctypes.c_int32),
+                ("word_offset", ctypes.c_int64), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class VdServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("bits_decoded", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("arena_used", ctypes.c_int64), ("error", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -116,6 +138,16 @@ def lib():
         L.vd_batch_plan_destroy.restype = None
         L.vd_decode_batch.argtypes = [P(vp), i32, P(VdPacket), i64, vp, vp, P(VdTune), vp]
         L.vd_decode_batch.restype = i32
+        L.vd_server_create.argtypes = [P(vp), P(vp), i32, P(VdServerConfig)]
+        L.vd_server_create.restype = i32
+        L.vd_server_submit.argtypes = [vp, i32, i32, vp, i64, i64, u32, ctypes.c_uint64]
+        L.vd_server_submit.restype = i32
+        L.vd_server_poll.argtypes = [vp, P(VdCompletion), i64, P(u32), i64]
+        L.vd_server_poll.restype = i64
+        L.vd_server_stats_get.argtypes = [vp, P(VdServerStats)]
+        L.vd_server_stats_get.restype = i32
+        L.vd_server_destroy.argtypes = [vp]
+        L.vd_server_destroy.restype = None
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -334,6 +366,70 @@ class BatchPlan:
         h, self.handle = getattr(self, "handle", None), None
         if h and _lib is not None:
             vd_batch_plan_destroy(h)
+
+    def __del__(self):
+        self.close()
+
+
+def vd_server_create(codes, cfg=None):
+    h = ctypes.c_void_p()
+    _check(lib().vd_server_create(ctypes.byref(h), _code_handles(codes), len(codes),
+                                  ctypes.byref(cfg) if cfg is not None else None))
+    return h.value
+
+
+def vd_server_submit(server, code_id, llr_type, host_llr, n_values, n_info, flags, tag):
+    """host_llr: a contiguous numpy array (int8 values, or packed 4-bit bytes)."""
+    _check(lib().vd_server_submit(ctypes.c_void_p(server), int(code_id), int(llr_type),
+                                  ctypes.c_void_p(host_llr.ctypes.data), int(n_values), int(n_info),
+                                  int(flags), ctypes.c_uint64(int(tag))))
+
+
+def vd_server_poll(server, max_completions=4096, words_cap=1 << 22):
+    """Returns a list of (VdCompletion, numpy uint32 words) for finished packets."""
+    import numpy as np
+    comp = (VdCompletion * max_completions)()
+    words = np.empty(words_cap, dtype=np.uint32)
+    n = lib().vd_server_poll(ctypes.c_void_p(server), comp, max_completions,
+                             words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), words_cap)
+    out = []
+    for i in range(n):
+        c = comp[i]
+        out.append((c, words[c.word_offset:c.word_offset + c.n_words].copy()))
+    return out
+
+
+def vd_server_stats_get(server) -> VdServerStats:
+    st = VdServerStats()
+    _check(lib().vd_server_stats_get(ctypes.c_void_p(server), ctypes.byref(st)))
+    return st
+
+
+def vd_server_destroy(server) -> None:
+    if server:
+        lib().vd_server_destroy(ctypes.c_void_p(server))
+
+
+class Server:
+    """Owning wrapper of a vd_server (continuous-batching decoder)."""
+
+    def __init__(self, codes, cfg=None):
+        self.codes = list(codes)
+        self.handle = vd_server_create(self.codes, cfg)
+
+    def submit(self, code_id, llr_type, host_llr, n_values, n_info, flags, tag):
+        vd_server_submit(self.handle, code_id, llr_type, host_llr, n_values, n_info, flags, tag)
+
+    def poll(self, max_completions=4096, words_cap=1 << 22):
+        return vd_server_poll(self.handle, max_completions, words_cap)
+
+    def stats(self):
+        return vd_server_stats_get(self.handle)
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            vd_server_destroy(h)
 
     def __del__(self):
         self.close()

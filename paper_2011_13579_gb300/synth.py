@@ -262,3 +262,35 @@ def uneven_packets(n_packets: int = 65536, index: int = 0, lo: int = 96, hi: int
     out_words = (n_info + 31) // 32
     out_off = np.concatenate([[0], np.cumsum(out_words)[:-1]]).astype(np.int64)
     return PacketBatch(n_info, rate_id, ebn0, llr_off, n_kept, out_off, llr, bits, bit_off)
+
+
+@dataclass
+class ServingPacket:
+    code_id: int          # 0: K=7 r1/2, 1: K=7 r3/4 (punctured), 2: K=9 r1/3
+    n_info: int
+    ebn0_db: float
+    llr_s8: np.ndarray    # kept values, int8
+    bits: np.ndarray
+
+
+SERVING_CODES = ((7, K7_GENS, None), (7, K7_GENS, PUNCT_R34), (9, K9_GENS, None))
+
+
+def serving_packets(n_packets: int, index: int = 0, punctured_share: float = 0.5):
+    """Serving mix: payloads uniform in 40..1500 bytes (n_info = 8 x bytes),
+    80% K=7 171/133 (a share of them punctured to r3/4), 20% K=9 557/663/711,
+    Eb/N0 uniform in 1..6 dB, terminated, int8 LLRs."""
+    rng = rng_for(5, index)
+    out = []
+    for _ in range(n_packets):
+        nbytes = int(rng.integers(40, 1501))
+        n = 8 * nbytes
+        if rng.random() < 0.8:
+            cid = 1 if rng.random() < punctured_share else 0
+        else:
+            cid = 2
+        K, gens, pat = SERVING_CODES[cid]
+        e = float(rng.uniform(1.0, 6.0))
+        st = make_stream(rng, K, gens, n, e, True, pattern=pat)
+        out.append(ServingPacket(cid, n, e, st.s8(), st.bits))
+    return out

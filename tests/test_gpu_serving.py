@@ -1,0 +1,121 @@
+"""Continuous-batching server: every packet decoded in the mix equals the
+same packet decoded alone (same frames, integer arithmetic: bit for bit),
+a subset equals the CPU oracle, and admission by device memory holds packets
+back without losing any when the arena is small."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2011_13579_gb300 as vd  # noqa: E402
+from paper_2011_13579_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vd.build()
+    yield
+
+
+def make_codes():
+    return [vd.Code(K, gens, puncture=None if pat is None else pat.tolist())
+            for (K, gens, pat) in synth.SERVING_CODES]
+
+
+def serve_all(server, pkts, timeout_s=60.0):
+    for i, p in enumerate(pkts):
+        server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, p.n_info, vd.VD_TERMINATED, i)
+    got, recs = {}, {}
+    t_end = time.time() + timeout_s
+    while len(got) < len(pkts) and time.time() < t_end:
+        for c, w in server.poll():
+            assert c.status == vd.VD_OK
+            got[c.tag] = w
+            recs[c.tag] = (c.submit_ns, c.admit_ns, c.done_ns)
+        time.sleep(0.001)
+    assert len(got) == len(pkts), f"only {len(got)} of {len(pkts)} packets completed"
+    return got, recs
+
+
+def alone(codes, p):
+    K = synth.SERVING_CODES[p.code_id][0]
+    F, V = (256, 42) if K == 7 else (512, 64)
+    f = min(p.n_info, F)
+    llr = torch.from_numpy(p.llr_s8.view(np.uint8)).cuda()
+    out = vd.decode(codes[p.code_id], llr, p.n_info, f, V, terminated=True)
+    return out.cpu().numpy().view(np.uint32), f, V
+
+
+@pytest.mark.parametrize("arena_mb,streams,max_batch", [(64, 3, 4096), (2, 2, 16), (8, 4, 64)])
+def test_mix_equals_alone_and_oracle(arena_mb, streams, max_batch):
+    codes = make_codes()
+    cfg = vd.VdServerConfig()
+    cfg.device_bytes = arena_mb << 20
+    cfg.n_streams = streams
+    cfg.max_batch = max_batch
+    server = vd.Server(codes, cfg)
+    pkts = synth.serving_packets(400, index=arena_mb)
+    got, recs = serve_all(server, pkts)
+    st = server.stats()
+    assert st.completed == len(pkts) and st.pending == 0 and st.error == 0
+    assert st.batches >= (2 if max_batch < 400 else 1)
+    for i, p in enumerate(pkts):
+        want, f, v = alone(codes, p)
+        assert np.array_equal(got[i], want), i
+        s, a, d = recs[i]
+        assert s <= a <= d
+        if i % 25 == 0:
+            K, gens, pat = synth.SERVING_CODES[p.code_id]
+            oc = oracle.Code(K, gens, puncture=pat)
+            T = p.n_info + K - 1
+            full = oracle.depuncture(oc, p.llr_s8.astype(np.int32), T)
+            assert np.array_equal(got[i], oracle.decode(oc, full, p.n_info, f, v, terminated=True)), i
+    server.close()
+
+
+def test_arrivals_while_busy_overlap():
+    """Packets submitted while earlier batches run are admitted into later
+    batches (more than one batch), and all results match decoding alone."""
+    codes = make_codes()
+    cfg = vd.VdServerConfig()
+    cfg.n_streams = 3
+    cfg.max_batch = 32
+    server = vd.Server(codes, cfg)
+    pkts = synth.serving_packets(300, index=77)
+    got = {}
+    for i, p in enumerate(pkts):
+        server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, p.n_info, vd.VD_TERMINATED, i)
+        if i % 20 == 0:
+            time.sleep(0.0005)
+            for c, w in server.poll():
+                got[c.tag] = w
+    t_end = time.time() + 60
+    while len(got) < len(pkts) and time.time() < t_end:
+        for c, w in server.poll():
+            got[c.tag] = w
+        time.sleep(0.001)
+    assert len(got) == len(pkts)
+    assert server.stats().batches > 2
+    for i in range(0, len(pkts), 7):
+        want, _, _ = alone(codes, pkts[i])
+        assert np.array_equal(got[i], want), i
+    server.close()
+
+
+def test_submit_validation():
+    codes = make_codes()
+    server = vd.Server(codes)
+    p = synth.serving_packets(1, index=5)[0]
+    with pytest.raises(vd.VdError):
+        server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size - 1, p.n_info, vd.VD_TERMINATED, 0)
+    with pytest.raises(vd.VdError):
+        server.submit(9, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, p.n_info, vd.VD_TERMINATED, 0)
+    with pytest.raises(vd.VdError):
+        server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, 20000, vd.VD_TERMINATED, 0)
+    server.close()
