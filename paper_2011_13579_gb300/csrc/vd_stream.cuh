@@ -613,14 +613,15 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     // process blocks of 16 registers (block pairs when the
                     // butterfly partner is in another block) and pack each
                     // block as soon as it is complete
+                    constexpr int PB = PH >= 4 ? (1 << (PH - 4)) : 0;   // partner block bit
 #pragma unroll
                     for (int blk = 0; blk < NR / 16; ++blk) {
-                        if (PH >= 4 && (blk & (1 << (PH - 4)))) continue;
+                        if (blk & PB) continue;
 #pragma unroll
                         for (int r = 16 * blk; r < 16 * blk + 16; ++r)
                             if (!(r & (1 << PH))) butterfly(r);
                         pack_block(blk);
-                        if (PH >= 4) pack_block(blk | (1 << (PH - 4)));
+                        if (PB) pack_block(blk | PB);
                     }
                 } else {
 #pragma unroll
@@ -682,7 +683,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                         lo_w[i] = (wd[i] & e1) | (~wd[i] & e0);
                     }
                 } else if constexpr (PH < LR) {
-                    constexpr int wb = 1 << (PH - 5);   // word-index bit (NR >= 64)
+                    constexpr int wb = PH >= 5 ? (1 << (PH - 5)) : 0;   // word-index bit (NR >= 64)
 #pragma unroll
                     for (int i = 0; i < NW; ++i) {
                         const int base = (i / WPF) * WPF, w = i % WPF;
