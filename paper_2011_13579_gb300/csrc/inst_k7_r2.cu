@@ -1,18 +1,16 @@
-// Radix-2 kernel instantiations for the K=7 code (generators 171/133).
+// Kernel instantiations: K=7 (171/133), radix 2, 1/2/4 lanes per frame pair.
 #include "vd_variants.cuh"
 
 namespace vd {
 
-using V_k7_r2 = Variants<7, 2, GENS_K7, false, 1, 2, 4>;
-
-cudaError_t launch_stream_k7_r2(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st) {
-    return V_k7_r2::stream(lanes, p, blocks, st);
-}
-cudaError_t launch_batch_k7_r2(int lanes, const BatchParams &p, int64_t blocks, cudaStream_t st) {
-    return V_k7_r2::batch(lanes, p, blocks, st);
-}
-cudaError_t occupancy_k7_r2(int lanes, int *blocks_per_sm) {
-    return V_k7_r2::occupancy(lanes, blocks_per_sm);
-}
+template cudaError_t launch_stream_v<7, false, 1>(const StreamParams &, int64_t, cudaStream_t);
+template cudaError_t launch_batch_v<7, false, 1>(const BatchParams &, int64_t, cudaStream_t);
+template cudaError_t occupancy_v<7, false, 1>(int *);
+template cudaError_t launch_stream_v<7, false, 2>(const StreamParams &, int64_t, cudaStream_t);
+template cudaError_t launch_batch_v<7, false, 2>(const BatchParams &, int64_t, cudaStream_t);
+template cudaError_t occupancy_v<7, false, 2>(int *);
+template cudaError_t launch_stream_v<7, false, 4>(const StreamParams &, int64_t, cudaStream_t);
+template cudaError_t launch_batch_v<7, false, 4>(const BatchParams &, int64_t, cudaStream_t);
+template cudaError_t occupancy_v<7, false, 4>(int *);
 
 }  // namespace vd

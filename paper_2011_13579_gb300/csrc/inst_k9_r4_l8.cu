@@ -1,0 +1,10 @@
+// Kernel instantiations: K=9 (557/663/711), radix 4, 8 lanes per frame pair.
+#include "vd_variants.cuh"
+
+namespace vd {
+
+template cudaError_t launch_stream_v<9, true, 8>(const StreamParams &, int64_t, cudaStream_t);
+template cudaError_t launch_batch_v<9, true, 8>(const BatchParams &, int64_t, cudaStream_t);
+template cudaError_t occupancy_v<9, true, 8>(int *);
+
+}  // namespace vd

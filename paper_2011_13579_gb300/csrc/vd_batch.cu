@@ -112,6 +112,7 @@ struct vd_batch_group {
     int64_t n_pairs, n_tasks;
     int32_t wpad_cap;
     int64_t blocks;
+    int32_t threads;      // block size
     vd::PacketDesc *d_pk;
     vd::PairRef *d_pairs;
     uint32_t *d_surv;
@@ -260,13 +261,14 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
             free_plan(pl);
             return fail(VD_EUNSUPPORTED, "no batch kernel with %d lanes for K=%d", g.lanes, K);
         }
+        g.threads = vd::kThreads;
         int bps = 0;
         cudaError_t e = kind == vd::KIND_K7_R2 ? vd::batch_occupancy_k7(g.lanes, g.r4, &bps)
                                                : vd::batch_occupancy_k9(g.lanes, g.r4, &bps);
         if (e != cudaSuccess || bps < 1) { free_plan(pl); return cuda_fail(e, "occupancy query"); }
         g.blocks = (int64_t)n_sm * bps;
         const int ppw = 32 / g.lanes;
-        const int64_t slots = g.blocks * (vd::kThreads / 32);
+        const int64_t slots = g.blocks * (g.threads / 32);
         const int U = g.geom.U;
         auto wpad_of = [&](int64_t W) { return ((W + U - 1) / U) * U; };
 
@@ -340,10 +342,10 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
         g.n_pairs = (int64_t)pairs.size();
         g.n_tasks = (g.n_pairs + ppw - 1) / ppw;
         g.wpad_cap = frs.empty() ? U : (int32_t)frs.front().wpad;
-        const int64_t tasks_blocks = (g.n_tasks * 32 + vd::kThreads - 1) / vd::kThreads;
+        const int64_t tasks_blocks = (g.n_tasks * 32 + g.threads - 1) / g.threads;
         g.blocks = std::max<int64_t>(1, std::min(g.blocks, tasks_blocks));
         // two survivor buffers per resident warp: one being written, one being traced back
-        g.surv_bytes = 2u * (size_t)g.blocks * vd::kThreads * (size_t)g.wpad_cap * g.geom.NW * 4u;
+        g.surv_bytes = 2u * (size_t)g.blocks * g.threads * (size_t)g.wpad_cap * g.geom.NW * 4u;
         if ((st = upload(&g.d_pk, pds, cs)) != VD_OK || (st = upload(&g.d_pairs, pairs, cs)) != VD_OK) {
             pl->groups.push_back(g);
             free_plan(pl);
@@ -462,7 +464,7 @@ extern "C" vd_status vd_batch_plan_info(const vd_batch_plan *pl, vd_batch_info *
         info->scratch_bytes += (int64_t)g.surv_bytes;
         info->lanes = g.lanes;
         info->radix = g.r4 ? 4 : 2;
-        info->resident_warps += g.blocks * (vd::kThreads / 32);
+        info->resident_warps += g.blocks * (g.threads / 32);
     }
     info->scratch_bytes += (int64_t)pl->llr_int_bytes;
     return VD_OK;

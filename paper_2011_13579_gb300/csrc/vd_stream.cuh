@@ -126,10 +126,11 @@ __device__ __forceinline__ void static_for(Fn &&fn) {
 
 // LLR chunk loading in two steps so the loads of chunk c+1 are in flight while
 // chunk c is decoded: fetch() issues the aligned 32-bit loads of bytes
-// [vb, vb + 4*UW) of the stream, finish() re-aligns them with funnel shifts.
-// A chunk that is not wholly inside [lo, hi) (the first chunk of a padded
-// frame, or a frame at a stream edge) is assembled byte by byte in finish()
-// with zeros outside the range.
+// [vb, vb + 4*UW) relative to the frame's first byte `base`, finish()
+// re-aligns them with funnel shifts.  A chunk that is not wholly inside the
+// frame's bytes [0, hi) (the first chunk of a padded frame) is assembled byte
+// by byte in finish() with zeros outside the range.  Offsets are 32-bit: a
+// frame spans far fewer than 2^31 bytes.
 template <int UW>
 struct ChunkRaw {
     uint32_t raw[UW + 1];
@@ -138,11 +139,10 @@ struct ChunkRaw {
 };
 
 template <int UW>
-__device__ __forceinline__ void fetch_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
-                                            ChunkRaw<UW> &c) {
-    c.fast = vb >= lo && vb + 4 * UW <= hi;
+__device__ __forceinline__ void fetch_chunk(const int8_t *base, int32_t vb, int32_t hi, ChunkRaw<UW> &c) {
+    c.fast = vb >= 0 && vb + 4 * UW <= hi;
     if (c.fast) {
-        const uintptr_t addr = reinterpret_cast<uintptr_t>(llr) + (uintptr_t)vb;
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(base) + (uintptr_t)(uint32_t)vb;
         const uint32_t mis = (uint32_t)(addr & 3u);
         const uint32_t *p = reinterpret_cast<const uint32_t *>(addr - mis);
 #pragma unroll
@@ -155,7 +155,7 @@ __device__ __forceinline__ void fetch_chunk(const int8_t *llr, int64_t vb, int64
 }
 
 template <int UW>
-__device__ __forceinline__ void finish_chunk(const int8_t *llr, int64_t vb, int64_t lo, int64_t hi,
+__device__ __forceinline__ void finish_chunk(const int8_t *base, int32_t vb, int32_t hi,
                                              const ChunkRaw<UW> &c, uint32_t (&w)[UW]) {
     if (c.fast) {
 #pragma unroll
@@ -166,8 +166,8 @@ __device__ __forceinline__ void finish_chunk(const int8_t *llr, int64_t vb, int6
             uint32_t x = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int64_t pos = vb + 4 * i + k;
-                if (pos >= lo && pos < hi) x |= (uint32_t)(uint8_t)llr[pos] << (8 * k);
+                const int32_t pos = vb + 4 * i + k;
+                if (pos >= 0 && pos < hi) x |= (uint32_t)(uint8_t)base[pos] << (8 * k);
             }
             w[i] = x;
         }
@@ -207,8 +207,9 @@ __host__ __device__ constexpr uint32_t bitk_mask(int k) {
 struct TbState {
     uint32_t *out[2];        // packed output of each frame's stream
     const uint32_t *surv;    // this lane's survivor words (stage stride 32 * NW words)
+    uint64_t oacc[2];        // decoded bits not yet stored: bit i = stage (lowest emitted + i)
     uint32_t R[2];           // current register of each frame (traceback state)
-    uint32_t oacc[2];        // output bits being assembled
+    int32_t onb[2];          // number of bits in oacc
     int32_t t0;              // first stage of the next group; finished when t0 < tau_store
     int32_t tau_store;
     int32_t tauo[2], taue[2];
@@ -279,8 +280,9 @@ struct Traceback {
         cp_async_wait<1>();
         const uint32_t *slot = stg + s.slot * SLOT_WORDS;
         const int t0 = s.t0;
-        uint32_t R0 = s.R[0], R1 = s.R[1], o0 = s.oacc[0], o1 = s.oacc[1];
-        const int tauo0 = s.tauo[0], tauo1 = s.tauo[1], taue0 = s.taue[0], taue1 = s.taue[1];
+        const int tl = t0 - (G - 1);   // lowest stage of the group
+        uint32_t Rh[2] = {s.R[0], s.R[1]};
+        const uint32_t Rs[2] = {Rh[0], Rh[1]};
         auto words = [&](int g, uint32_t (&wd)[NW]) {
             const uint32_t *p = slot + (g * 32 + wlane) * NW;
             if constexpr (NW == 1) {
@@ -296,82 +298,80 @@ struct Traceback {
                 }
             }
         };
-        auto decision = [&](const uint32_t (&wd)[NW], int h, uint32_t Rh) -> uint32_t {
+        // The survivor word of register R in frame h, rotated right so that
+        // R's decision bit lands at bit position ph.
+        auto rotated = [&](const uint32_t (&wd)[NW], int h, uint32_t R, int ph) -> uint32_t {
             uint32_t word, bit;
             if constexpr (NR >= 32) {
-                word = pick<WPF>(&wd[h * WPF], (Rh >> 5) & (uint32_t)(WPF - 1));
-                bit = Rh & 31u;
+                word = pick<WPF>(&wd[h * WPF], (R >> 5) & (uint32_t)(WPF - 1));
+                bit = R;
             } else {
                 word = wd[0];
-                bit = (Rh & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
+                bit = (R & (uint32_t)(NR - 1)) + 16u * (uint32_t)h;
             }
-            return (word >> bit) & 1u;
+            return __funnelshift_r(word, word, bit - (uint32_t)ph);
         };
-        auto owner_bits = [&](uint32_t bits, uint32_t Rh) -> uint32_t {
-            if constexpr (L > 1) return __shfl_sync(gmask, bits, grp_base + (int)(Rh >> LR));
-            else return bits;
-        };
-        auto emit = [&](int h, int t, uint32_t u) {
-            uint32_t &o = h ? o1 : o0;
-            if (t < (h ? taue1 : taue0)) {
-                o = (o << 1) | u;
-                const int tabs = t + s.toff[h];
-                if ((tabs & 31) == 0) {
-                    if (lane == (L > 1 ? h : 0)) s.out[h][tabs >> 5] = o;
-                    o = 0;
-                }
-            }
+        auto owner = [&](uint32_t x, uint32_t R) -> uint32_t {
+            if constexpr (L > 1) return __shfl_sync(gmask, x, grp_base + (int)(R >> LR));
+            else return x;
         };
         if constexpr (!RADIX4) {
             static_for<G>([&](auto gc) {
                 constexpr int g = decltype(gc)::value;
                 constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // group starts at -1 mod (K-1)
-                const int t = t0 - g;
                 uint32_t wd[NW];
                 words(g, wd);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    uint32_t &Rh = h ? R1 : R0;
-                    if (t >= (h ? tauo1 : tauo0)) {
-                        const uint32_t d = owner_bits(decision(wd, h, Rh), Rh);
-                        const uint32_t u = (Rh >> ph) & 1u;
-                        Rh = (Rh & ~(1u << ph)) | (d << ph);
-                        emit(h, t, u);
-                    }
+                    const uint32_t t = owner(rotated(wd, h, Rh[h], ph), Rh[h]);
+                    Rh[h] = (Rh[h] & ~(1u << ph)) | (t & (1u << ph));
                 }
             });
         } else {
-            // pairs (t, t-1): t is the second stage of a pair
+            // pairs (t, t-1): t is the second stage of a pair; both decisions
+            // of register R sit at the same bit position in the two words
             static_for<G / 2>([&](auto gc) {
                 constexpr int g = 2 * decltype(gc)::value;
                 constexpr int ph2 = ((NB - 1 - g) % NB + NB) % NB;
                 constexpr int ph1 = ((NB - 2 - g) % NB + NB) % NB;
-                const int t = t0 - g;
+                constexpr uint32_t m2 = 1u << ph2, m1 = 1u << ph1;
                 uint32_t w2[NW], w1[NW];
                 words(g, w2);
                 words(g + 1, w1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    uint32_t &Rh = h ? R1 : R0;
-                    if (t >= (h ? tauo1 : tauo0)) {
-                        const uint32_t b2 = decision(w2, h, Rh);
-                        const uint32_t b1 = decision(w1, h, Rh);   // same position
-                        const uint32_t bb = owner_bits(b2 | (b1 << 1), Rh);
-                        const uint32_t u2 = (Rh >> ph2) & 1u;
-                        const uint32_t m = (Rh & ~(1u << ph2)) | ((bb & 1u) << ph2);
-                        emit(h, t, u2);
-                        if (t - 1 >= (h ? tauo1 : tauo0)) {
-                            const uint32_t u1 = (m >> ph1) & 1u;
-                            Rh = (m & ~(1u << ph1)) | (((bb >> 1) & 1u) << ph1);
-                            emit(h, t - 1, u1);
-                        } else {
-                            Rh = m;
-                        }
-                    }
+                    const uint32_t t2 = rotated(w2, h, Rh[h], ph2);
+                    const uint32_t t1 = rotated(w1, h, Rh[h], ph1);
+                    const uint32_t t = owner((t2 & m2) | (t1 & ~m2), Rh[h]);
+                    Rh[h] = (Rh[h] & ~(m2 | m1)) | (t & (m2 | m1));
                 }
             });
         }
-        s.R[0] = R0; s.R[1] = R1; s.oacc[0] = o0; s.oacc[1] = o1;
+        // Each bit position of R is replaced once per group, so the group's
+        // decoded bits (the input bit of each stage's state) are the bits of
+        // R at the start of the group: stage tl + i is bit i.
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lo = tl > s.tauo[h] ? tl : s.tauo[h];
+            const int hi = (t0 + 1) < s.taue[h] ? (t0 + 1) : s.taue[h];
+            if (hi > lo) {
+                const int m = hi - lo;
+                const uint64_t bits = (uint64_t)((Rs[h] >> (lo - tl)) & ((1u << m) - 1u));
+                uint64_t acc = (s.oacc[h] << m) | bits;
+                int nb = s.onb[h] + m;
+                const int a = lo + s.toff[h];              // stream stage of bit 0
+                const int wb = (a + nb - 1) & ~31;         // first stage of the top word
+                if (a <= wb) {
+                    if (lane == (L > 1 ? h : 0)) s.out[h][wb >> 5] = (uint32_t)(acc >> (wb - a));
+                    nb = wb - a;
+                    acc &= (1ull << nb) - 1ull;
+                }
+                s.oacc[h] = acc;
+                s.onb[h] = nb;
+            }
+        }
+        s.R[0] = Rh[0];
+        s.R[1] = Rh[1];
         // refill the consumed slot with the group two ahead, then advance
         issue(s, t0 - 2 * G, stg + s.slot * SLOT_WORDS, wlane);
         s.t0 = t0 - G;
@@ -454,9 +454,11 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
 #pragma unroll
     for (int r = 0; r < NR; ++r) P[r] = SEED0;   // all-equal: unknown start
 
-    const int64_t vb0 = (fa[0] - tau0[0]) * BETA, vb1 = (fa[1] - tau0[1]) * BETA;
-    const int64_t lo0 = fa[0] * BETA, hi0 = valid[0] ? fb[0] * BETA : lo0;
-    const int64_t lo1 = fa[1] * BETA, hi1 = valid[1] ? fb[1] * BETA : lo1;
+    // LLR bytes relative to each frame's first stage; stage tau of the pair is
+    // frame stage tau - tau0
+    const int8_t *fbase0 = ft[0].llr + fa[0] * BETA, *fbase1 = ft[1].llr + fa[1] * BETA;
+    const int32_t hi0 = valid[0] ? (int32_t)W[0] * BETA : 0, hi1 = valid[1] ? (int32_t)W[1] * BETA : 0;
+    int32_t vb0 = -tau0[0] * BETA, vb1 = -tau0[1] * BETA;   // offset of the chunk being fetched
 
     auto store_words = [&](int tau, const uint32_t (&wd)[NW]) {
         uint32_t *dst = surv + ((size_t)tau * 32 + wlane) * NW;
@@ -479,19 +481,22 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const int nchunks = Wpad / U;
     ChunkRaw<UW> nx0, nx1;
     if (nchunks > 0) {
-        fetch_chunk<UW>(ft[0].llr, vb0, lo0, hi0, nx0);
-        fetch_chunk<UW>(ft[1].llr, vb1, lo1, hi1, nx1);
+        fetch_chunk<UW>(fbase0, vb0, hi0, nx0);
+        fetch_chunk<UW>(fbase1, vb1, hi1, nx1);
     }
     for (int c = 0; c < nchunks; ++c) {
         uint32_t cw0[UW], cw1[UW];
         {
             const ChunkRaw<UW> cur0 = nx0, cur1 = nx1;
+            const int32_t cb0 = vb0, cb1 = vb1;
+            vb0 += U * BETA;
+            vb1 += U * BETA;
             if (c + 1 < nchunks) {
-                fetch_chunk<UW>(ft[0].llr, vb0 + (int64_t)(c + 1) * U * BETA, lo0, hi0, nx0);
-                fetch_chunk<UW>(ft[1].llr, vb1 + (int64_t)(c + 1) * U * BETA, lo1, hi1, nx1);
+                fetch_chunk<UW>(fbase0, vb0, hi0, nx0);
+                fetch_chunk<UW>(fbase1, vb1, hi1, nx1);
             }
-            finish_chunk<UW>(ft[0].llr, vb0 + (int64_t)c * U * BETA, lo0, hi0, cur0, cw0);
-            finish_chunk<UW>(ft[1].llr, vb1 + (int64_t)c * U * BETA, lo1, hi1, cur1, cw1);
+            finish_chunk<UW>(fbase0, cb0, hi0, cur0, cw0);
+            finish_chunk<UW>(fbase1, cb1, hi1, cur1, cw1);
         }
         uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
 
@@ -775,6 +780,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     tb.R[0] = R[0];
     tb.R[1] = R[1];
     tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.onb[0] = tb.onb[1] = 0;
     tb.t0 = Wpad - 1;
     tb.tau_store = tau_store;
 #pragma unroll

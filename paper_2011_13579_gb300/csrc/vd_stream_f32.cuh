@@ -94,27 +94,30 @@ __device__ __forceinline__ bool forward_pair_f32(const FrameTask (&ft)[2], uint3
 #pragma unroll
         for (int r = 0; r < NR; ++r) P[h][r] = 0.0f;
 
-    const int64_t vb0 = (fa[0] - tau0[0]) * BETA * 2, vb1 = (fa[1] - tau0[1]) * BETA * 2;
-    const int64_t lo0 = fa[0] * BETA * 2, hi0 = valid[0] ? fb[0] * BETA * 2 : lo0;
-    const int64_t lo1 = fa[1] * BETA * 2, hi1 = valid[1] ? fb[1] * BETA * 2 : lo1;
-    const int8_t *llr0 = ft[0].llr, *llr1 = ft[1].llr;
+    // fp16 LLR bytes relative to each frame's first stage
+    const int8_t *fbase0 = ft[0].llr + fa[0] * BETA * 2, *fbase1 = ft[1].llr + fa[1] * BETA * 2;
+    const int32_t hi0 = valid[0] ? (int32_t)W[0] * BETA * 2 : 0, hi1 = valid[1] ? (int32_t)W[1] * BETA * 2 : 0;
+    int32_t vb0 = -tau0[0] * BETA * 2, vb1 = -tau0[1] * BETA * 2;
 
     const int nchunks = Wpad / U;
     ChunkRaw<UW> nx0, nx1;
     if (nchunks > 0) {
-        fetch_chunk<UW>(llr0, vb0, lo0, hi0, nx0);
-        fetch_chunk<UW>(llr1, vb1, lo1, hi1, nx1);
+        fetch_chunk<UW>(fbase0, vb0, hi0, nx0);
+        fetch_chunk<UW>(fbase1, vb1, hi1, nx1);
     }
     for (int c = 0; c < nchunks; ++c) {
         uint32_t cw0[UW], cw1[UW];
         {
             const ChunkRaw<UW> cur0 = nx0, cur1 = nx1;
+            const int32_t cb0 = vb0, cb1 = vb1;
+            vb0 += U * BETA * 2;
+            vb1 += U * BETA * 2;
             if (c + 1 < nchunks) {
-                fetch_chunk<UW>(llr0, vb0 + (int64_t)(c + 1) * U * BETA * 2, lo0, hi0, nx0);
-                fetch_chunk<UW>(llr1, vb1 + (int64_t)(c + 1) * U * BETA * 2, lo1, hi1, nx1);
+                fetch_chunk<UW>(fbase0, vb0, hi0, nx0);
+                fetch_chunk<UW>(fbase1, vb1, hi1, nx1);
             }
-            finish_chunk<UW>(llr0, vb0 + (int64_t)c * U * BETA * 2, lo0, hi0, cur0, cw0);
-            finish_chunk<UW>(llr1, vb1 + (int64_t)c * U * BETA * 2, lo1, hi1, cur1, cw1);
+            finish_chunk<UW>(fbase0, cb0, hi0, cur0, cw0);
+            finish_chunk<UW>(fbase1, cb1, hi1, cur1, cw1);
         }
         static_for<U>([&](auto Sc) {
             constexpr int S = decltype(Sc)::value;
@@ -253,6 +256,7 @@ __device__ __forceinline__ bool forward_pair_f32(const FrameTask (&ft)[2], uint3
     tb.R[0] = R[0];
     tb.R[1] = R[1];
     tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.onb[0] = tb.onb[1] = 0;
     tb.t0 = Wpad - 1;
     tb.tau_store = tau_store;
 #pragma unroll
