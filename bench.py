@@ -32,6 +32,7 @@ N_INFO = 1 << 24
 F, V = 256, 42
 EBN0S = (1.0, 2.0, 3.0, 4.0, 5.0, 6.0)
 K, BETA = 7, 2
+PLAIN_STREAMS = 32
 
 
 def workload_config(radix, lanes, path="batch"):
@@ -279,11 +280,266 @@ def run_gpu(args, rank, world):
 
     if plan is not None:
         plan.close()
-    return {"ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
+    packets = None
+    if rank == 0 and args.packets > 0:
+        packets = run_packets(args, dev, s)
+    return {"packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "ber_6db": ber6, "n_sm": torch.cuda.get_device_properties(dev).multi_processor_count}
+
+
+def run_packets(args, dev, s):
+    """Batched persistent decode vs one launch per packet on the uneven-packet
+    workload: 65,536 terminated K=7 packets, log-uniform 96..12,000 info bits,
+    r1/2, r2/3, r3/4 in equal shares, Eb/N0 ~ U(2, 7) dB, int8 kept LLRs.
+    The batched form is one autotuned plan replayed from a CUDA graph; the
+    plain form is one vd_decode call per packet at the f/v/radix the plan
+    chose, so both must give the same bits."""
+    import ctypes
+    import torch
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+
+    batch = synth.uneven_packets(args.packets)
+    pats = (None, synth.PUNCT_R23, synth.PUNCT_R34)
+    codes = [vd.Code(K, synth.K7_GENS, puncture=None if p is None else p.tolist()) for p in pats]
+    n = batch.n_packets
+    pk = {"code_id": batch.rate_id.astype(np.int32), "llr_type": np.zeros(n, np.int32),
+          "llr_offset": batch.llr_offset, "n_info": batch.n_info,
+          "flags": np.full(n, vd.VD_TERMINATED, np.uint32), "f": np.zeros(n, np.int32),
+          "v": np.zeros(n, np.int32), "out_word_offset": batch.out_word_offset}
+    plan = vd.BatchPlan(codes, pk, stream=s)
+    info = plan.info()
+    f, v = plan.packet_tune()
+    llr = torch.from_numpy(batch.llr_s8.view(np.uint8)).to(dev)
+    nw = int(batch.out_word_offset[-1] + (batch.n_info[-1] + 31) // 32)
+    out_b = torch.empty(nw, dtype=torch.int32, device=dev)
+    out_p = torch.full((nw,), -1, dtype=torch.int32, device=dev)
+    bits = int(batch.n_info.sum())
+
+    for _ in range(max(3, args.warmup)):
+        plan.launch(llr, out_b, stream=s, graph=True)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 50))
+    a.record(s)
+    for _ in range(reps):
+        plan.launch(llr, out_b, stream=s, graph=True)
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    ms_b = a.elapsed_time(b) / reps
+    plan.status(stream=s)
+
+    # plain: one vd_decode per packet (raw pointers, the library's default kernel
+    # shape), round-robin over PLAIN_STREAMS streams so independent packets overlap
+    L = vd.lib()
+    llr_base, out_base = llr.data_ptr(), out_p.data_ptr()
+    handles = [c.handle for c in codes]
+    side = [torch.cuda.Stream(dev) for _ in range(PLAIN_STREAMS)]
+    shs = [ctypes.c_void_p(x.cuda_stream) for x in side]
+    radix = int(info.radix)
+    order = np.argsort(-batch.n_info, kind="stable")   # warm-up: largest first sizes the scratch once
+
+    def plain_pass(idx):
+        for k, i in enumerate(idx):
+            st = L.vd_decode(ctypes.c_void_p(handles[batch.rate_id[i]]),
+                             ctypes.c_void_p(llr_base + int(batch.llr_offset[i])), vd.VD_LLR_S8,
+                             int(batch.n_info[i]), int(f[i]), int(v[i]), radix, vd.VD_TERMINATED,
+                             ctypes.c_void_p(out_base + 4 * int(batch.out_word_offset[i])), None, None,
+                             shs[k % PLAIN_STREAMS])
+            if st != 0:
+                raise RuntimeError(f"vd_decode failed on packet {i}: {L.vd_last_error().decode()}")
+
+    plain_pass(np.repeat(order[:4], PLAIN_STREAMS))   # every stream's scratch sized by the largest packets
+    torch.cuda.synchronize(dev)
+    a.record(s)
+    for x in side:
+        x.wait_event(a)
+    plain_pass(range(n))
+    for x in side:
+        e = torch.cuda.Event()
+        e.record(x)
+        s.wait_event(e)
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    ms_p = a.elapsed_time(b)
+    for x in side:
+        vd.vd_sync(x)
+    identical = bool(torch.equal(out_b, out_p))
+    plan.close()
+    return {"workload": f"{n} terminated K=7 packets, log-uniform 96..12000 info bits, r1/2 r2/3 r3/4 "
+                        "equal shares, Eb/N0 U(2,7) dB, int8 kept LLRs",
+            "info_bits": bits, "batched_gbps": bits / (ms_b / 1e3) / 1e9, "batched_ms": ms_b,
+            "plain_gbps": bits / (ms_p / 1e3) / 1e9, "plain_ms": ms_p, "speedup": ms_p / ms_b,
+            "identical_output": identical,
+            "batched_form": "one persistent launch per step (autotuned plan, CUDA-graph replay)",
+            "plain_form": f"one vd_decode call per packet, same f/v/radix, round-robin over {PLAIN_STREAMS} "
+                          "CUDA streams (as many hardware queues), issued from Python via ctypes",
+            "tune": {"radix": radix, "lanes": int(info.lanes), "resident_warps": int(info.resident_warps),
+                     "f_median": int(np.median(f)), "v_median": int(np.median(v))}}
+
+
+def run_serving(args):
+    """Continuous-batching server under open-loop Poisson load.  A pool of
+    serving packets (payloads U{40..1500} bytes; 80% K=7 171/133, half of
+    those punctured to r3/4; 20% K=9 557/663/711; Eb/N0 U(1, 6) dB; int8;
+    terminated) is first replayed all at once to measure the server's peak
+    packet rate; then for each offered load x the packets arrive as a Poisson
+    process of rate x * peak (the aggregate of 256 streams), cycling through
+    the pool.  Latency is host submit to completion seen by the server."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+
+    pool = synth.serving_packets(args.serving_pool, index=0)
+    fl = synth.flatten_packets(pool)
+    n = len(pool)
+    codes = [vd.Code(Kc, gens, puncture=None if pat is None else pat.tolist())
+             for (Kc, gens, pat) in synth.SERVING_CODES]
+    server = vd.Server(codes)
+    types = np.zeros(n, np.int32)
+    flags = np.full(n, vd.VD_TERMINATED, np.uint32)
+    # warm-up, then the closed-loop peak (every packet offered at t = 0)
+    server.replay(fl["code_id"][:256], types[:256], fl["llr"], fl["llr_offset"][:256], fl["n_values"][:256],
+                  fl["n_info"][:256], flags[:256], np.zeros(256, np.int64), timeout_ms=120000)
+    _, ref_words, span = server.replay(fl["code_id"], types, fl["llr"], fl["llr_offset"], fl["n_values"],
+                                       fl["n_info"], flags, np.zeros(n, np.int64), timeout_ms=300000,
+                                       word_offset=fl["word_offset"])
+    pool_bits = int(fl["n_info"].sum())
+    peak_pps = n / (span / 1e9)
+    points = []
+    rng = np.random.Generator(np.random.PCG64(2011135790 + 500))
+    consistent = True
+    for x in args.serving_loads:
+        rate = x * peak_pps
+        m = int(min(max(n, rate * args.serving_seconds), args.serving_max_packets))
+        idx = np.arange(m) % n
+        arr = synth.poisson_arrivals(rng, m, rate)
+        lat, words, span = server.replay(fl["code_id"][idx], types[idx], fl["llr"], fl["llr_offset"][idx],
+                                         fl["n_values"][idx], fl["n_info"][idx], flags[idx], arr,
+                                         timeout_ms=600000, word_offset=fl["word_offset"][idx])
+        consistent &= bool(np.array_equal(words[:ref_words.size], ref_words))
+        bits = int(fl["n_info"][idx].sum())
+        points.append({"offered": x, "packets": m, "offered_pps": rate,
+                       "gbps": bits / (span / 1e9) / 1e9,
+                       "p50_ms": float(np.percentile(lat, 50)) / 1e6,
+                       "p99_ms": float(np.percentile(lat, 99)) / 1e6})
+    st = server.stats()
+    server.close()
+    return {"workload": f"pool of {n} packets, payload U(40..1500) B, 80% K=7 r1/2 (half punctured to r3/4), "
+                        "20% K=9 r1/3, Eb/N0 U(1,6) dB, int8, terminated; Poisson arrivals (256 streams "
+                        "aggregated) at x * peak",
+            "peak_pps": peak_pps, "peak_gbps": pool_bits / (n / peak_pps) / 1e9,
+            "points": points, "same_bits_at_every_load": consistent, "batches": int(st.batches),
+            "latency": "host submit -> completion seen by the server (steady clock)"}
+
+
+def run_bm_gate(dev, s):
+    """Branch metrics (Eq. BM) of the (2,1,7) code on CUDA cores vs tensor cores
+    (mma.sync m16n8k32 s8 plus a transpose into the decoder's layout), on an
+    L2-resident LLR block: 3 x 128 threads per SM x 152 SMs of frame pairs x
+    256 stages.  Both kernels fold the same metrics into the same checksum."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    n_pairs, n_stages = n_sm * 3 * 128, 256
+    rng = np.random.Generator(np.random.PCG64(2011135790 + 700))
+    words = torch.from_numpy(rng.integers(0, 2 ** 32, size=n_pairs * n_stages, dtype=np.uint64)
+                             .astype(np.uint32).view(np.int32)).to(dev)
+    res = {}
+    sums = []
+    for variant, name in ((0, "cuda_core"), (1, "tensor_core_mma_sync")):
+        cs = torch.zeros(n_pairs, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            vd.vd_bm_gate(variant, words, n_pairs, n_stages, cs, stream=s)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(20):
+            vd.vd_bm_gate(variant, words, n_pairs, n_stages, cs, stream=s)
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / 20
+        res[name] = {"ms": ms, "ps_per_pair_stage": ms * 1e9 / (n_pairs * n_stages)}
+        sums.append(cs.cpu().numpy())
+    res["same_metrics"] = bool(np.array_equal(sums[0], sums[1]))
+    res["tensor_over_cuda_time"] = res["tensor_core_mma_sync"]["ms"] / res["cuda_core"]["ms"]
+    res["workload"] = f"{n_pairs} frame pairs x {n_stages} stages, int8 LLRs, L2-resident"
+    return res
+
+
+def run_precision(args):
+    """Precision study on the (3,1,9) 557/663/711 code: 2^24 information bits
+    per Eb/N0 in 0..4 dB, f=512, v=64, decoded on the GPU three ways — int8 and
+    4-bit LLRs with integer metrics (checked bit for bit against the int64
+    oracle on the same values) and fp16 LLRs with fp32 metrics (disagreement
+    with the FP64 oracle on the same fp16 values, every disagreeing frame
+    checked against the tie margin) — and BER of each form against the true
+    bits, with the FP64 oracle on the unquantised LLRs (2y/sigma^2) as the
+    BER reference.  GPU throughput per form is the time of one vd_decode."""
+    import torch
+    import oracle
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+    oracle.build()
+    n, f, v = args.precision_bits, 512, 64
+    threads = len(os.sched_getaffinity(0))
+    code = vd.Code(9, synth.K9_GENS)
+    oc = oracle.Code(9, synth.K9_GENS)
+    s = torch.cuda.Stream()
+    points = []
+
+    def gpu(buf, ltype, lanes):
+        out = vd.decode(code, buf, n, f, v, llr_type=ltype, lanes=lanes, stream=s)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        vd.decode(code, buf, n, f, v, llr_type=ltype, lanes=lanes, stream=s, out=out)
+        b.record(s)
+        torch.cuda.synchronize()
+        vd.vd_sync(s)
+        return oracle.unpack_bits(out.cpu().numpy().view(np.uint32), n), n / (a.elapsed_time(b) / 1e3) / 1e9
+
+    for e in args.precision_ebn0:
+        st = synth.precision_stream(e, n_info=n)
+        T = st.T
+        pt = {"ebn0_db": e}
+        ref = oracle.unpack_bits(oracle.decode_f64(oc, st.f64().reshape(T, 3), n, f, v, threads=threads)[0], n)
+        ber_ref = float(np.mean(ref != st.bits))
+        pt["ber_fp64_unquantised"] = ber_ref
+        q8 = st.s8()
+        g8, t8 = gpu(torch.from_numpy(q8.view(np.uint8)).cuda(), vd.VD_LLR_S8, 0)
+        o8 = oracle.unpack_bits(oracle.decode(oc, q8.reshape(T, 3).astype(np.int32), n, f, v, threads=threads), n)
+        pt["int8"] = {"gbps": t8, "bit_exact_vs_oracle": bool(np.array_equal(g8, o8)),
+                      "ber": float(np.mean(g8 != st.bits)), "ber_delta": float(np.mean(g8 != st.bits)) - ber_ref}
+        q4 = st.s4()
+        g4, t4 = gpu(torch.from_numpy(synth.pack_s4(q4)).cuda(), vd.VD_LLR_S4, 0)
+        o4 = oracle.unpack_bits(oracle.decode(oc, q4.reshape(T, 3).astype(np.int32), n, f, v, threads=threads), n)
+        pt["int4"] = {"gbps": t4, "bit_exact_vs_oracle": bool(np.array_equal(g4, o4)),
+                      "ber": float(np.mean(g4 != st.bits)), "ber_delta": float(np.mean(g4 != st.bits)) - ber_ref}
+        h = st.f16()
+        gh, th = gpu(torch.from_numpy(h.view(np.uint16)).cuda(), vd.VD_LLR_F16, 8)
+        ow, gap, mx = oracle.decode_f64(oc, h.astype(np.float64).reshape(T, 3), n, f, v, threads=threads)
+        oh = oracle.unpack_bits(ow, n)
+        dis_frames, unexplained = 0, 0
+        bad = np.nonzero(gh != oh)[0]
+        frames = np.unique(bad // f)
+        for fr in frames:
+            a = max(0, fr * f - v)
+            b = min(T, (fr + 1) * f + v)
+            tau = 4.0 * (b - a) * 2.0 ** -24 * max(mx[fr], 1.0)
+            dis_frames += 1
+            unexplained += int(not gap[fr] <= tau)
+        pt["fp16_fp32"] = {"gbps": th, "disagree_bits": int(bad.size), "disagree_rate": float(bad.size / n),
+                           "disagree_frames": dis_frames, "frames_outside_tie_margin": unexplained,
+                           "ber": float(np.mean(gh != st.bits)), "ber_delta": float(np.mean(gh != st.bits)) - ber_ref}
+        points.append(pt)
+        print(json.dumps(pt), file=sys.stderr, flush=True)
+    return {"workload": f"K=9 r1/3 (557,663,711), {n} info bits per Eb/N0, f=512, v=64, unterminated",
+            "ber_floor": 100.0 / n, "oracle_threads": threads, "points": points}
 
 
 def kernel_only(args):
@@ -325,13 +581,28 @@ def main():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--path", default="batch", choices=["batch", "stream"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bm-gate", action="store_true", help="skip the branch-metric CUDA/tensor-core gate")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-loads", type=lambda t: [float(x) for x in t.split(",")] if t else [],
+                    default=[0.1, 0.5, 0.9], help="offered loads (fractions of peak); empty: skip serving")
+    ap.add_argument("--serving-pool", type=int, default=8192)
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-max-packets", type=int, default=400000)
+    ap.add_argument("--workload", default="stream", choices=["stream", "precision"],
+                    help="precision: the K=9 precision study (int8 / 4-bit / fp16) instead of the bench line")
+    ap.add_argument("--precision-bits", type=int, default=1 << 24)
+    ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
+                    default=[0.0, 1.0, 2.0, 3.0, 4.0])
+    ap.add_argument("--packets", type=int, default=65536,
+                    help="packets of the batched-vs-plain comparison (0: skip it)")
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: only W+K launches of one stream decode (for profilers)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    # one hardware queue per stream of the one-launch-per-packet comparison
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(PLAIN_STREAMS))
 
     if args.impl == "reference":
         # the reference arm is the plain CPU oracle; rank 0 alone runs it
@@ -362,6 +633,10 @@ def main():
         dist.init_process_group("nccl")
     import paper_2011_13579_gb300 as vd
     vd.build()
+    if args.workload == "precision":
+        if rank == 0:
+            print(json.dumps({"precision_study": run_precision(args)}), flush=True)
+        return
     if args.mode == "kernel":
         kernel_only(args)
         return
@@ -419,6 +694,13 @@ def main():
         "clocks": r["clocks"],
         "ber_6db": r["ber_6db"],
     }
+    if r.get("packets"):
+        line["batched_vs_plain"] = r["packets"]
+    if world == 1 and args.serving_loads:
+        line["serving"] = run_serving(args)
+    if world == 1 and not args.no_bm_gate:
+        import torch
+        line["bm_gate"] = run_bm_gate(torch.device("cuda", 0), torch.cuda.current_stream())
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_oracle_run(args.cpu_seconds)

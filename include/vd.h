@@ -276,6 +276,45 @@ vd_status vd_server_stats_get(vd_server *server, vd_server_stats *out);
 void vd_server_destroy(vd_server *server);
 
 /*
+ * vd_server_replay — open-loop trace replay against a server (a load
+ * generator for latency measurement; the paper has no counterpart).
+ *
+ * Submits packet i (tag i) when arrival_ns[i] nanoseconds (nondecreasing)
+ * have passed since the call started, polling completions meanwhile, until
+ * all n packets have completed.  Packet i: code_id[i], llr_type[i],
+ * n_values[i] values at host_llr + llr_offset[i] bytes, n_info[i], flags[i].
+ * Outputs: latency_ns[i] = completion time - submit time (host steady clock,
+ * -1 if unfinished); if words is not NULL, packet i's decoded words at
+ * words + word_offset[i]; *span_ns (if not NULL) = last completion - first
+ * submit.  The server must be idle (nothing submitted and unpolled).
+ * Errors: VD_EINVAL (bad arguments, busy server), a submit error,
+ * VD_ECUDA (device error), VD_ETIMEOUT after timeout_ms (> 0) — packets then
+ * still in the server stay there until it is destroyed.
+ */
+vd_status vd_server_replay(vd_server *server, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                           const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                           const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
+                           int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
+                           const int64_t *word_offset, int64_t *span_ns);
+
+/*
+ * vd_bm_gate — the measurement behind the choice of CUDA cores over tensor
+ * cores for the branch metrics (Eq. BM; the paper computes them as the
+ * product of the code's +-1 output patterns with the LLRs, Sec. V).  For the
+ * (2,1,7) code, computes the four branch metrics of every (stage, frame pair)
+ * with variant 0 = CUDA-core 16x2 arithmetic (the decoder's form) or
+ * 1 = mma.sync m16n8k32 s8 tensor-core products plus a shared-memory
+ * transpose into the decoder's per-lane layout.
+ *   d_llr:      [n_stages][n_pairs] words, bytes l0, l1 of frame 0 then of frame 1 (int8)
+ *   n_pairs:    a positive multiple of 32; n_stages > 0
+ *   d_checksum: [n_pairs] words, a fold of every metric of the pair (same for both variants)
+ *   d_metrics:  NULL, or [n_stages][4][n_pairs] words: pattern x (bit b set: -l_b) as s16x2
+ * Asynchronous on stream; VD_EINVAL on bad arguments, VD_ECUDA on launch failure.
+ */
+vd_status vd_bm_gate(int variant, const void *d_llr, int64_t n_pairs, int32_t n_stages,
+                     uint32_t *d_checksum, uint32_t *d_metrics, void *stream);
+
+/*
  * Waits for the stream, then reads and clears the library's device status
  * word.  VD_EBOUNDS if a kernel refused work that would have overrun its
  * scratch since the last check (the affected outputs are not written).

@@ -25,7 +25,7 @@ __all__ = [
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_bm_gate", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -148,6 +148,11 @@ def lib():
         L.vd_server_stats_get.restype = i32
         L.vd_server_destroy.argtypes = [vp]
         L.vd_server_destroy.restype = None
+        L.vd_server_replay.argtypes = [vp, i64, P(i32), P(i32), vp, P(i64), P(i64), P(i64), P(u32), P(i64),
+                                       i64, P(i64), P(u32), P(i64), P(i64)]
+        L.vd_server_replay.restype = i32
+        L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
+        L.vd_bm_gate.restype = i32
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -223,6 +228,14 @@ def vd_scratch_bytes(handle, n_info, f, v, radix=2, tune=None) -> int:
 def vd_sync(stream=None) -> None:
     """Waits for the stream and raises VdError if a kernel reported a device-side error."""
     _check(lib().vd_sync(_stream_handle(stream)))
+
+
+def vd_bm_gate(variant, llr_words, n_pairs, n_stages, checksum, metrics=None, stream=None) -> None:
+    """Branch-metric gate kernels (0: CUDA cores, 1: tensor cores) on device tensors."""
+    _check(lib().vd_bm_gate(int(variant), ctypes.c_void_p(llr_words.data_ptr()), int(n_pairs), int(n_stages),
+                            ctypes.c_void_p(checksum.data_ptr()),
+                            ctypes.c_void_p(metrics.data_ptr()) if metrics is not None else None,
+                            _stream_handle(stream)))
 
 
 def vd_release_scratch() -> None:
@@ -410,6 +423,44 @@ def vd_server_destroy(server) -> None:
         lib().vd_server_destroy(ctypes.c_void_p(server))
 
 
+def vd_server_replay(server, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, arrival_ns,
+                     timeout_ms=0, word_offset=None):
+    """Open-loop replay: packet i is submitted arrival_ns[i] ns after the start.
+    host_llr is one contiguous uint8/int8 numpy array holding every packet's
+    values at llr_offset[i].  Returns (latency_ns int64 array, words uint32
+    array or None, span_ns)."""
+    import numpy as np
+    n = len(n_info)
+    a_code = np.ascontiguousarray(code_id, dtype=np.int32)
+    a_type = np.ascontiguousarray(llr_type, dtype=np.int32)
+    a_off = np.ascontiguousarray(llr_offset, dtype=np.int64)
+    a_nv = np.ascontiguousarray(n_values, dtype=np.int64)
+    a_ni = np.ascontiguousarray(n_info, dtype=np.int64)
+    a_fl = np.ascontiguousarray(flags, dtype=np.uint32)
+    a_arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    host = np.ascontiguousarray(host_llr)
+    lat = np.empty(n, dtype=np.int64)
+    words = None
+    a_wo = None
+    if word_offset is not None:
+        a_wo = np.ascontiguousarray(word_offset, dtype=np.int64)
+        total = int((a_wo + (a_ni + 31) // 32).max()) if n else 0
+        words = np.zeros(max(total, 1), dtype=np.uint32)
+    span = ctypes.c_int64(0)
+    P = ctypes.POINTER
+
+    def ptr(a, t):
+        return a.ctypes.data_as(P(t)) if a is not None else None
+
+    _check(lib().vd_server_replay(ctypes.c_void_p(server), n, ptr(a_code, ctypes.c_int32),
+                                  ptr(a_type, ctypes.c_int32), ctypes.c_void_p(host.ctypes.data),
+                                  ptr(a_off, ctypes.c_int64), ptr(a_nv, ctypes.c_int64),
+                                  ptr(a_ni, ctypes.c_int64), ptr(a_fl, ctypes.c_uint32),
+                                  ptr(a_arr, ctypes.c_int64), int(timeout_ms), ptr(lat, ctypes.c_int64),
+                                  ptr(words, ctypes.c_uint32), ptr(a_wo, ctypes.c_int64), ctypes.byref(span)))
+    return lat, words, int(span.value)
+
+
 class Server:
     """Owning wrapper of a vd_server (continuous-batching decoder)."""
 
@@ -425,6 +476,9 @@ class Server:
 
     def stats(self):
         return vd_server_stats_get(self.handle)
+
+    def replay(self, *args, **kw):
+        return vd_server_replay(self.handle, *args, **kw)
 
     def close(self):
         h, self.handle = getattr(self, "handle", None), None

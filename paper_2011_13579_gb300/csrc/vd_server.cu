@@ -562,3 +562,66 @@ extern "C" void vd_server_destroy(vd_server *s) {
         for (Req *r : sl.reqs) delete r;
     free_server(s);
 }
+
+extern "C" vd_status vd_server_replay(vd_server *s, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                                      const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                                      const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
+                                      int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
+                                      const int64_t *word_offset, int64_t *span_ns) {
+    if (!s) return fail(VD_EINVAL, "server is NULL");
+    if (n < 0) return fail(VD_EINVAL, "n < 0");
+    if (n > 0 && (!code_id || !llr_type || !host_llr || !llr_offset || !n_values || !n_info || !flags ||
+                  !arrival_ns || !latency_ns))
+        return fail(VD_EINVAL, "a packet array is NULL");
+    if (words && !word_offset) return fail(VD_EINVAL, "words given without word_offset");
+    for (int64_t i = 1; i < n; ++i)
+        if (arrival_ns[i] < arrival_ns[i - 1]) return fail(VD_EINVAL, "arrival_ns must be nondecreasing");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stats.submitted != s->stats.completed || !s->done_q.empty())
+            return fail(VD_EINVAL, "replay needs an idle server (packets in flight or not polled)");
+    }
+    const int64_t cap_comp = 4096;
+    const int64_t cap_words = cap_comp * ((int64_t)s->cfg.max_packet_bits + 31) / 32;
+    std::vector<vd_completion> comp((size_t)cap_comp);
+    std::vector<uint32_t> wbuf((size_t)cap_words);
+    for (int64_t i = 0; i < n; ++i) latency_ns[i] = -1;
+    const uint8_t *base = (const uint8_t *)host_llr;
+    const int64_t t0 = now_ns();
+    const int64_t deadline = timeout_ms > 0 ? t0 + timeout_ms * 1000000 : INT64_MAX;
+    int64_t next = 0, done = 0, first_submit = INT64_MAX, last_done = t0;
+    while (done < n) {
+        const int64_t now = now_ns();
+        if (now > deadline) {
+            if (span_ns) *span_ns = last_done - (first_submit == INT64_MAX ? t0 : first_submit);
+            return fail(VD_ETIMEOUT, "replay: %lld of %lld packets done after %lld ms", (long long)done,
+                        (long long)n, (long long)timeout_ms);
+        }
+        while (next < n && arrival_ns[next] <= now - t0) {
+            const vd_status st = vd_server_submit(s, code_id[next], llr_type[next], base + llr_offset[next],
+                                                  n_values[next], n_info[next], flags[next], (uint64_t)next);
+            if (st != VD_OK) return st;
+            ++next;
+        }
+        const int64_t k = vd_server_poll(s, comp.data(), cap_comp, wbuf.data(), cap_words);
+        for (int64_t j = 0; j < k; ++j) {
+            const vd_completion &c = comp[(size_t)j];
+            const int64_t i = (int64_t)c.tag;
+            if (i < 0 || i >= n) continue;
+            if (c.status != VD_OK) return fail(VD_ECUDA, "replay: the device reported an error");
+            latency_ns[i] = c.done_ns - c.submit_ns;
+            first_submit = std::min(first_submit, c.submit_ns);
+            last_done = std::max(last_done, c.done_ns);
+            if (words) memcpy(words + word_offset[i], wbuf.data() + c.word_offset, (size_t)c.n_words * 4);
+            ++done;
+        }
+        if (k == 0) {
+            // nothing finished: wait for the next arrival (spinning when it is close)
+            const int64_t wait = next < n ? arrival_ns[next] - (now_ns() - t0) : 20000;
+            if (wait > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+            else if (wait > 0) std::this_thread::yield();
+        }
+    }
+    if (span_ns) *span_ns = n ? last_done - first_submit : 0;
+    return VD_OK;
+}

@@ -294,3 +294,22 @@ def serving_packets(n_packets: int, index: int = 0, punctured_share: float = 0.5
         st = make_stream(rng, K, gens, n, e, True, pattern=pat)
         out.append(ServingPacket(cid, n, e, st.s8(), st.bits))
     return out
+
+
+def flatten_packets(pkts):
+    """The packets' int8 values in one array with per-packet offsets, counts and
+    output word offsets (the layout the server's trace replay takes)."""
+    n_values = np.array([p.llr_s8.size for p in pkts], dtype=np.int64)
+    llr_offset = np.concatenate([[0], np.cumsum(n_values)[:-1]]).astype(np.int64)
+    n_info = np.array([p.n_info for p in pkts], dtype=np.int64)
+    words = (n_info + 31) // 32
+    word_offset = np.concatenate([[0], np.cumsum(words)[:-1]]).astype(np.int64)
+    llr = np.concatenate([p.llr_s8 for p in pkts]) if pkts else np.zeros(0, np.int8)
+    return {"code_id": np.array([p.code_id for p in pkts], dtype=np.int32), "llr": llr,
+            "llr_offset": llr_offset, "n_values": n_values, "n_info": n_info, "word_offset": word_offset}
+
+
+def poisson_arrivals(rng, n, rate_per_s):
+    """Arrival times (ns, from 0) of a Poisson process of the given rate."""
+    gaps = rng.exponential(1.0 / rate_per_s, size=n)
+    return np.floor(np.cumsum(gaps) * 1e9).astype(np.int64)

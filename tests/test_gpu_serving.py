@@ -119,3 +119,30 @@ def test_submit_validation():
     with pytest.raises(vd.VdError):
         server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, 20000, vd.VD_TERMINATED, 0)
     server.close()
+
+
+def test_replay_open_loop_matches_alone():
+    """Trace replay (Poisson arrivals): every packet completes with a positive
+    latency and decodes to the same bits as alone; a busy server is refused."""
+    codes = make_codes()
+    server = vd.Server(codes)
+    pkts = synth.serving_packets(300, index=91)
+    fl = synth.flatten_packets(pkts)
+    n = len(pkts)
+    arr = synth.poisson_arrivals(np.random.Generator(np.random.PCG64(5)), n, 20000.0)
+    lat, words, span = server.replay(fl["code_id"], np.zeros(n, np.int32), fl["llr"], fl["llr_offset"],
+                                     fl["n_values"], fl["n_info"], np.full(n, vd.VD_TERMINATED, np.uint32),
+                                     arr, timeout_ms=60000, word_offset=fl["word_offset"])
+    assert (lat > 0).all() and span > 0
+    for i in range(0, n, 5):
+        want, _, _ = alone(codes, pkts[i])
+        o = int(fl["word_offset"][i])
+        assert np.array_equal(words[o:o + want.size], want), i
+    # a packet left unpolled makes the server busy for a replay
+    p = pkts[0]
+    server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, p.n_info, vd.VD_TERMINATED, 0)
+    with pytest.raises(vd.VdError):
+        server.replay(fl["code_id"][:1], np.zeros(1, np.int32), fl["llr"], fl["llr_offset"][:1],
+                      fl["n_values"][:1], fl["n_info"][:1], np.full(1, vd.VD_TERMINATED, np.uint32),
+                      np.zeros(1, np.int64))
+    server.close()
