@@ -65,11 +65,12 @@ def ops_per_bit(f=F, v=V, k=K):
 
 
 def kernel_source_hash():
-    """Hash of the stream kernel's sources: a traffic figure measured on other
+    """Hash of the decode kernels' sources: a traffic figure measured on other
     sources does not describe this kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("paper_2011_13579_gb300/csrc/vd_stream.cuh", "paper_2011_13579_gb300/csrc/vd_device.cuh"):
+    for f in ("paper_2011_13579_gb300/csrc/vd_stream.cuh", "paper_2011_13579_gb300/csrc/vd_device.cuh",
+              "paper_2011_13579_gb300/csrc/vd_batch.cuh"):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
