@@ -604,13 +604,18 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 P[r] = addmax_u16x2(own, d_own, add_u16x2(oth, d_oth));
                 X[r] = imad(own, m1, oth) + e;
             };
-            auto pack_block = [&](int blk) {   // 16 registers -> acc[blk]
+            // 16 registers -> acc[blk]: each prmt turns the decision bits of
+            // registers r1, r1+8 (both halves) into bytes 0x00/0xFF; a depth-3
+            // tree of bitwise selects (one LOP3 each) then puts register
+            // 16 blk + kk at bit kk of every byte
+            auto pack_block = [&](int blk) {
+                uint32_t t[8];
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int r1 = 16 * blk + kk;
-                    const uint32_t t = prmt(X[r1], X[r1 + 8], 0xFDB9u);
-                    acc[blk] |= t & (0x01010101u << kk);
-                }
+                for (int kk = 0; kk < 8; ++kk) t[kk] = prmt(X[16 * blk + kk], X[16 * blk + kk + 8], 0xFDB9u);
+                auto sel = [](uint32_t a, uint32_t b, uint32_t m) { return (a & m) | (b & ~m); };
+                const uint32_t m0 = sel(t[0], t[1], 0x01010101u), m1 = sel(t[2], t[3], 0x04040404u);
+                const uint32_t m2 = sel(t[4], t[5], 0x10101010u), m3 = sel(t[6], t[7], 0x40404040u);
+                acc[blk] = sel(sel(m0, m1, 0x03030303u), sel(m2, m3, 0x30303030u), 0x0F0F0F0Fu);
             };
 
             if constexpr (NR >= 16) {
