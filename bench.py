@@ -45,16 +45,18 @@ def workload_config(radix, lanes, path="batch"):
             "l2": "inputs larger than L2 (192 MiB cycled per step)"}
 
 
-def stream_plan(vd, code, n_streams, radix, lanes, stream):
-    """The six streams as six packets of one batch plan (f=256, v=42)."""
+def stream_plan(vd, code, n_streams, radix, lanes, stream, first=0):
+    """Streams first .. first+n_streams-1 of the arena as the packets of one
+    batch plan (f=256, v=42); offsets are into the whole arena."""
     tune = vd.VdTune()
     tune.radix = radix
     tune.lanes = lanes
+    idx = np.arange(first, first + n_streams, dtype=np.int64)
     pk = {"code_id": np.zeros(n_streams, np.int32), "llr_type": np.zeros(n_streams, np.int32),
-          "llr_offset": np.arange(n_streams, dtype=np.int64) * BETA * N_INFO,
+          "llr_offset": idx * BETA * N_INFO,
           "n_info": np.full(n_streams, N_INFO, np.int64), "flags": np.zeros(n_streams, np.uint32),
           "f": np.full(n_streams, F, np.int32), "v": np.full(n_streams, V, np.int32),
-          "out_word_offset": np.arange(n_streams, dtype=np.int64) * (N_INFO // 32)}
+          "out_word_offset": idx * (N_INFO // 32)}
     return vd.BatchPlan([code], pk, tune=tune, stream=stream)
 
 
@@ -167,6 +169,19 @@ def cpu_oracle_run(seconds_budget=15.0, threads=None):
 
 # ------------------------------------------------------------------- GPU
 
+def whole_job_value(ms_local, bits_per_rank_step, steps, world, device=None):
+    """Whole-job throughput (Gbit/s) of `world` replicas: every rank's bits over
+    the slowest rank's time, taken with a MAX all-reduce.  Returns (ms, value)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, bits_per_rank_step * steps * world / (ms / 1e3) / 1e9
+
+
 def run_gpu(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -241,34 +256,72 @@ def run_gpu(args, rank, world):
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     clocks = sampler.stop() if sampler else None
 
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-
     bits_per_step = N_INFO * len(streams)
-    value = bits_per_step * args.steps * world / (ms / 1e3) / 1e9
+    ms, value = whole_job_value(ms, bits_per_step, args.steps, world, dev)
 
     # end to end through the public API with host buffers: pinned H2D of the
-    # step's LLRs, decode, D2H of the decoded words, all inside the timed region
+    # step's LLRs, decode, D2H of the decoded words, all inside the timed
+    # region.  The batch path pipelines: the streams are split into parts, each
+    # decoded by its own plan; part j's upload overlaps part j-1's decode (two
+    # decode streams, so one plan's last tasks overlap the next plan's first),
+    # and each part's words go back as soon as it is decoded.
     host_in = [torch.from_numpy(x).pin_memory() for x in streams]
     host_out = [torch.empty(nw, dtype=torch.int32).pin_memory() for _ in streams]
     e2e_steps = max(1, min(args.steps, 5))
+    parts = []
+    if plan is not None:
+        per = -(-len(streams) // max(1, args.e2e_parts))
+        for first in range(0, len(streams), per):
+            cnt = min(per, len(streams) - first)
+            parts.append((list(range(first, first + cnt)),
+                          stream_plan(vd, code, cnt, args.radix, args.lanes, s, first=first)))
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    comp = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s)
-    with torch.cuda.stream(s):
+    if parts:
+        for x in [up, down] + comp:
+            x.wait_event(e0)
+        done_prev = [None] * len(parts)
         for _ in range(e2e_steps):
-            for i in range(len(streams)):
-                llr_dev[i].copy_(host_in[i], non_blocking=True)
-            for i in range(launches_per_step):
-                one_launch(i)
-            for i in range(len(streams)):
-                host_out[i].copy_(outs[i], non_blocking=True)
+            for j, (idx, pl) in enumerate(parts):
+                if done_prev[j] is not None:
+                    up.wait_event(done_prev[j])        # the previous step's decode read these inputs
+                with torch.cuda.stream(up):
+                    for i in idx:
+                        llr_dev[i].copy_(host_in[i], non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(up)
+                cs = comp[j % 2]
+                cs.wait_event(ev_in)
+                pl.launch(arena, out_arena, stream=cs)
+                ev_done = torch.cuda.Event()
+                ev_done.record(cs)
+                done_prev[j] = ev_done
+                down.wait_event(ev_done)
+                with torch.cuda.stream(down):
+                    for i in idx:
+                        host_out[i].copy_(outs[i], non_blocking=True)
+        for x in [up, down] + comp:
+            ev = torch.cuda.Event()
+            ev.record(x)
+            s.wait_event(ev)
+    else:
+        with torch.cuda.stream(s):
+            for _ in range(e2e_steps):
+                for i in range(len(streams)):
+                    llr_dev[i].copy_(host_in[i], non_blocking=True)
+                for i in range(launches_per_step):
+                    one_launch(i)
+                for i in range(len(streams)):
+                    host_out[i].copy_(outs[i], non_blocking=True)
     e1.record(s)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
+    for _, pl in parts:
+        pl.close()
     e2e_value = bits_per_step * e2e_steps / (e2e_ms / 1e3) / 1e9
     h2d = sum(int(x.size) for x in streams)
     d2h = nw * 4 * len(streams)
@@ -287,7 +340,9 @@ def run_gpu(args, rank, world):
     return {"packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h),
+                    "form": (f"{len(parts)} batch plans; pinned uploads overlap decoding on two streams"
+                             if parts else "upload, decode, download in order on one stream")},
             "ber_6db": ber6, "n_sm": torch.cuda.get_device_properties(dev).multi_processor_count}
 
 
@@ -594,6 +649,8 @@ def main():
     ap.add_argument("--precision-bits", type=int, default=1 << 24)
     ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.0, 1.0, 2.0, 3.0, 4.0])
+    ap.add_argument("--e2e-parts", type=int, default=3,
+                    help="end-to-end leg: plans the streams are split into so uploads overlap decoding")
     ap.add_argument("--packets", type=int, default=65536,
                     help="packets of the batched-vs-plain comparison (0: skip it)")
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
