@@ -207,6 +207,10 @@ def run_gpu(args, rank, world):
         tune.lanes = args.lanes
     flags = 0
     plan = stream_plan(vd, code, len(streams), args.radix, args.lanes, s) if args.path == "batch" else None
+    shape = {"radix": args.radix, "lanes": args.lanes}
+    if plan is not None:
+        info = plan.info()   # lanes chosen by the plan's measured autotuner when --lanes is 0
+        shape = {"radix": int(info.radix), "lanes": int(info.lanes)}
 
     def one_launch(i):
         """Launch i of a step: one stream, or the whole batch."""
@@ -337,7 +341,7 @@ def run_gpu(args, rank, world):
     packets = None
     if rank == 0 and args.packets > 0:
         packets = run_packets(args, dev, s)
-    return {"packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
+    return {"shape": shape, "packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
@@ -438,14 +442,16 @@ def run_packets(args, dev, s):
                      "f_median": int(np.median(f)), "v_median": int(np.median(v))}}
 
 
-def run_serving(args):
+def run_serving(args, device_resident=False):
     """Continuous-batching server under open-loop Poisson load.  A pool of
     serving packets (payloads U{40..1500} bytes; 80% K=7 171/133, half of
     those punctured to r3/4; 20% K=9 557/663/711; Eb/N0 U(1, 6) dB; int8;
     terminated) is first replayed all at once to measure the server's peak
     packet rate; then for each offered load x the packets arrive as a Poisson
     process of rate x * peak (the aggregate of 256 streams), cycling through
-    the pool.  Latency is host submit to completion seen by the server."""
+    the pool.  Latency is host submit to completion seen by the server.
+    device_resident: the pool's values are uploaded once and submitted in
+    place (vd_server_submit_device), as from an upstream GPU stage."""
     import torch
     import paper_2011_13579_gb300 as vd
     from paper_2011_13579_gb300 import synth
@@ -456,12 +462,13 @@ def run_serving(args):
     codes = [vd.Code(Kc, gens, puncture=None if pat is None else pat.tolist())
              for (Kc, gens, pat) in synth.SERVING_CODES]
     server = vd.Server(codes)
+    src = torch.from_numpy(fl["llr"].view(np.uint8)).cuda() if device_resident else fl["llr"]
     types = np.zeros(n, np.int32)
     flags = np.full(n, vd.VD_TERMINATED, np.uint32)
     # warm-up, then the closed-loop peak (every packet offered at t = 0)
-    server.replay(fl["code_id"][:256], types[:256], fl["llr"], fl["llr_offset"][:256], fl["n_values"][:256],
+    server.replay(fl["code_id"][:256], types[:256], src, fl["llr_offset"][:256], fl["n_values"][:256],
                   fl["n_info"][:256], flags[:256], np.zeros(256, np.int64), timeout_ms=120000)
-    _, ref_words, span = server.replay(fl["code_id"], types, fl["llr"], fl["llr_offset"], fl["n_values"],
+    _, ref_words, span = server.replay(fl["code_id"], types, src, fl["llr_offset"], fl["n_values"],
                                        fl["n_info"], flags, np.zeros(n, np.int64), timeout_ms=300000,
                                        word_offset=fl["word_offset"])
     pool_bits = int(fl["n_info"].sum())
@@ -474,7 +481,7 @@ def run_serving(args):
         m = int(min(max(n, rate * args.serving_seconds), args.serving_max_packets))
         idx = np.arange(m) % n
         arr = synth.poisson_arrivals(rng, m, rate)
-        lat, words, span = server.replay(fl["code_id"][idx], types[idx], fl["llr"], fl["llr_offset"][idx],
+        lat, words, span = server.replay(fl["code_id"][idx], types[idx], src, fl["llr_offset"][idx],
                                          fl["n_values"][idx], fl["n_info"][idx], flags[idx], arr,
                                          timeout_ms=600000, word_offset=fl["word_offset"][idx])
         consistent &= bool(np.array_equal(words[:ref_words.size], ref_words))
@@ -485,7 +492,9 @@ def run_serving(args):
                        "p99_ms": float(np.percentile(lat, 99)) / 1e6})
     st = server.stats()
     server.close()
-    return {"workload": f"pool of {n} packets, payload U(40..1500) B, 80% K=7 r1/2 (half punctured to r3/4), "
+    return {"submission": "device-resident values, submitted in place" if device_resident
+            else "host values, copied at submit",
+            "workload": f"pool of {n} packets, payload U(40..1500) B, 80% K=7 r1/2 (half punctured to r3/4), "
                         "20% K=9 r1/3, Eb/N0 U(1,6) dB, int8, terminated; Poisson arrivals (256 streams "
                         "aggregated) at x * peak",
             "peak_pps": peak_pps, "peak_gbps": pool_bits / (n / peak_pps) / 1e9,
@@ -740,7 +749,8 @@ def main():
         "vs_baseline": None,
         "dtype": "u16x2",
         "data": "synthetic",
-        "config": {**workload_config(args.radix, args.lanes, args.path), "parallelism": f"replicas{world}"},
+        "config": {**workload_config(r["shape"]["radix"], r["shape"]["lanes"], args.path),
+                   "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "vd::batch_kernel" if args.path == "batch" else "vd::stream_kernel",
@@ -756,6 +766,7 @@ def main():
         line["batched_vs_plain"] = r["packets"]
     if world == 1 and args.serving_loads:
         line["serving"] = run_serving(args)
+        line["serving_device"] = run_serving(args, device_resident=True)
     if world == 1 and not args.no_bm_gate:
         import torch
         line["bm_gate"] = run_bm_gate(torch.device("cuda", 0), torch.cuda.current_stream())

@@ -59,7 +59,7 @@ typedef enum {
     VD_EINVAL = -1,        /* bad argument (message in vd_last_error) */
     VD_ENOMEM = -2,        /* device or host allocation failed */
     VD_ECUDA = -3,         /* a CUDA runtime call failed */
-    VD_EUNSUPPORTED = -4,  /* valid request this build has no kernel for */
+    VD_EUNSUPPORTED = -4,  /* valid request the library has no kernel for */
     VD_ETIMEOUT = -5,      /* a bounded device wait ran out */
     VD_EBOUNDS = -6        /* a device-side bounds check fired */
 } vd_status;
@@ -96,7 +96,7 @@ typedef struct vd_tune {
  * or a beta x period row-major 0/1 matrix (period 1..8, no all-zero column)
  * whose column t mod period says which outputs of stage t are transmitted.
  * On success *out owns a new object; on failure *out is NULL.
- * VD_EUNSUPPORTED: a code this build has no kernel for (see vd_code_supported).
+ * VD_EUNSUPPORTED: a code the library has no kernel for (see vd_code_supported).
  */
 vd_status vd_code_create(vd_code **out, int K, int beta, const uint32_t *gens_octal,
                          int rate_num, int rate_den, const uint8_t *puncture, int period);
@@ -104,7 +104,7 @@ vd_status vd_code_create(vd_code **out, int K, int beta, const uint32_t *gens_oc
 /* Frees a code object (NULL is ignored). */
 void vd_code_destroy(vd_code *code);
 
-/* 1 if this build has a decode kernel for (K, beta, generators), else 0. */
+/* 1 if the library has a decode kernel for (K, beta, generators), else 0. */
 int vd_code_supported(int K, int beta, const uint32_t *gens_octal);
 
 /*
@@ -175,6 +175,10 @@ typedef struct vd_batch_info {
  * decoded as one full-length frame; v = 42 for K=7, 64 for K=9, or tune->v),
  * sorts and pairs all frames, and uploads descriptors and work list (device
  * memory owned by the plan).  tune: NULL, or lanes / radix / f / v overrides.
+ * When tune is NULL or leaves radix (or lanes) at 0, the plan measures the
+ * candidate kernel shapes (radix 2 and 4; 1 or 2 lanes per frame pair for
+ * K=7, 4 or 8 for K=9) by running its own work list on zero LLRs on
+ * `stream`, and keeps the fastest; the shape never changes the decoded bits.
  * The arenas are given at launch.  Synchronises `stream` before returning.
  */
 vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *const *codes, int n_codes,
@@ -263,6 +267,14 @@ vd_status vd_server_create(vd_server **out, const vd_code *const *codes, int n_c
 vd_status vd_server_submit(vd_server *server, int code_id, int llr_type, const void *host_llr,
                            int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag);
 
+/* As vd_server_submit, for values already in device memory (an upstream
+ * stage on the GPU produced them): nothing is copied; the kernels read the
+ * caller's buffer in place, so it must stay valid and unchanged until the
+ * packet's completion has been polled.  Punctured / 4-bit packets are still
+ * expanded into the server's arena. */
+vd_status vd_server_submit_device(vd_server *server, int code_id, int llr_type, const void *d_llr,
+                                  int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag);
+
 /* Moves up to max_completions finished packets out: their records into comp
  * and their decoded words into words (capacity words_cap).  Returns the
  * number of records written (0 if none is ready). */
@@ -296,6 +308,14 @@ vd_status vd_server_replay(vd_server *server, int64_t n, const int32_t *code_id,
                            const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
                            int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
                            const int64_t *word_offset, int64_t *span_ns);
+
+/* vd_server_replay with the packets' values in device memory (d_llr +
+ * llr_offset[i] bytes), submitted with vd_server_submit_device. */
+vd_status vd_server_replay_device(vd_server *server, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                                  const void *d_llr, const int64_t *llr_offset, const int64_t *n_values,
+                                  const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
+                                  int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
+                                  const int64_t *word_offset, int64_t *span_ns);
 
 /*
  * vd_bm_gate — the measurement behind the choice of CUDA cores over tensor

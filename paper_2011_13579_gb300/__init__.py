@@ -25,7 +25,7 @@ __all__ = [
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_server_replay", "vd_bm_gate", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -151,6 +151,10 @@ def lib():
         L.vd_server_replay.argtypes = [vp, i64, P(i32), P(i32), vp, P(i64), P(i64), P(i64), P(u32), P(i64),
                                        i64, P(i64), P(u32), P(i64), P(i64)]
         L.vd_server_replay.restype = i32
+        L.vd_server_replay_device.argtypes = L.vd_server_replay.argtypes
+        L.vd_server_replay_device.restype = i32
+        L.vd_server_submit_device.argtypes = [vp, i32, i32, vp, i64, i64, u32, ctypes.c_uint64]
+        L.vd_server_submit_device.restype = i32
         L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
         L.vd_bm_gate.restype = i32
         L.vd_sync.argtypes = [vp]
@@ -423,12 +427,21 @@ def vd_server_destroy(server) -> None:
         lib().vd_server_destroy(ctypes.c_void_p(server))
 
 
+def vd_server_submit_device(server, code_id, llr_type, d_llr, n_values, n_info, flags, tag):
+    """d_llr: a contiguous CUDA tensor (or a device address) holding the packet's values."""
+    addr = d_llr if isinstance(d_llr, int) else d_llr.data_ptr()
+    _check(lib().vd_server_submit_device(ctypes.c_void_p(server), int(code_id), int(llr_type),
+                                         ctypes.c_void_p(addr), int(n_values), int(n_info), int(flags),
+                                         ctypes.c_uint64(int(tag))))
+
+
 def vd_server_replay(server, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, arrival_ns,
                      timeout_ms=0, word_offset=None):
     """Open-loop replay: packet i is submitted arrival_ns[i] ns after the start.
     host_llr is one contiguous uint8/int8 numpy array holding every packet's
-    values at llr_offset[i].  Returns (latency_ns int64 array, words uint32
-    array or None, span_ns)."""
+    values at llr_offset[i] — or a CUDA tensor, whose packets are then
+    submitted in place (vd_server_replay_device).  Returns (latency_ns int64
+    array, words uint32 array or None, span_ns)."""
     import numpy as np
     n = len(n_info)
     a_code = np.ascontiguousarray(code_id, dtype=np.int32)
@@ -438,7 +451,14 @@ def vd_server_replay(server, code_id, llr_type, host_llr, llr_offset, n_values, 
     a_ni = np.ascontiguousarray(n_info, dtype=np.int64)
     a_fl = np.ascontiguousarray(flags, dtype=np.uint32)
     a_arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
-    host = np.ascontiguousarray(host_llr)
+    device = hasattr(host_llr, "is_cuda") and host_llr.is_cuda
+    if device:
+        if not host_llr.is_contiguous():
+            raise ValueError("the device LLR tensor must be contiguous")
+        base = ctypes.c_void_p(host_llr.data_ptr())
+    else:
+        host = np.ascontiguousarray(host_llr)
+        base = ctypes.c_void_p(host.ctypes.data)
     lat = np.empty(n, dtype=np.int64)
     words = None
     a_wo = None
@@ -452,12 +472,11 @@ def vd_server_replay(server, code_id, llr_type, host_llr, llr_offset, n_values, 
     def ptr(a, t):
         return a.ctypes.data_as(P(t)) if a is not None else None
 
-    _check(lib().vd_server_replay(ctypes.c_void_p(server), n, ptr(a_code, ctypes.c_int32),
-                                  ptr(a_type, ctypes.c_int32), ctypes.c_void_p(host.ctypes.data),
-                                  ptr(a_off, ctypes.c_int64), ptr(a_nv, ctypes.c_int64),
-                                  ptr(a_ni, ctypes.c_int64), ptr(a_fl, ctypes.c_uint32),
-                                  ptr(a_arr, ctypes.c_int64), int(timeout_ms), ptr(lat, ctypes.c_int64),
-                                  ptr(words, ctypes.c_uint32), ptr(a_wo, ctypes.c_int64), ctypes.byref(span)))
+    fn = lib().vd_server_replay_device if device else lib().vd_server_replay
+    _check(fn(ctypes.c_void_p(server), n, ptr(a_code, ctypes.c_int32), ptr(a_type, ctypes.c_int32), base,
+              ptr(a_off, ctypes.c_int64), ptr(a_nv, ctypes.c_int64), ptr(a_ni, ctypes.c_int64),
+              ptr(a_fl, ctypes.c_uint32), ptr(a_arr, ctypes.c_int64), int(timeout_ms), ptr(lat, ctypes.c_int64),
+              ptr(words, ctypes.c_uint32), ptr(a_wo, ctypes.c_int64), ctypes.byref(span)))
     return lat, words, int(span.value)
 
 
@@ -479,6 +498,9 @@ class Server:
 
     def replay(self, *args, **kw):
         return vd_server_replay(self.handle, *args, **kw)
+
+    def submit_device(self, code_id, llr_type, d_llr, n_values, n_info, flags, tag):
+        vd_server_submit_device(self.handle, code_id, llr_type, d_llr, n_values, n_info, flags, tag)
 
     def close(self):
         h, self.handle = getattr(self, "handle", None), None

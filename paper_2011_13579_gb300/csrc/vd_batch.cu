@@ -59,7 +59,7 @@ __global__ void prep_batch_kernel(const PrepBatchParams p) {
         int64_t k = jb.src_off + (t / c.period) * c.kept_per_period + c.kept_prefix[ph];
         for (int b = 0; b < c.beta; ++b) {
             int8_t x = 0;
-            if (c.punct[b][ph]) x = batch_kept_value(p.src, k++, jb.llr_type);
+            if (c.punct[b][ph]) x = batch_kept_value(jb.src ? jb.src : p.src, k++, jb.llr_type);
             p.dst[jb.dst_off + t * c.beta + b] = x;
         }
     }
@@ -169,6 +169,137 @@ vd_status upload(T **dst, const std::vector<T> &src, cudaStream_t st) {
     return VD_OK;
 }
 
+// Kernel shape of a group: geometry, resident blocks and scratch for
+// (lanes, radix); the pairs and descriptors do not depend on it.
+bool shape_group(vd_batch_group &g, int lanes, bool r4, int n_sm) {
+    g.lanes = lanes;
+    g.r4 = r4;
+    g.threads = vd::kThreads;
+    if (!kind_geom(g.kind, lanes, r4, &g.geom)) return false;
+    int bps = 0;
+    const cudaError_t e = g.kind == vd::KIND_K7_R2 ? vd::batch_occupancy_k7(lanes, r4, &bps)
+                                                   : vd::batch_occupancy_k9(lanes, r4, &bps);
+    if (e != cudaSuccess || bps < 1) { cudaGetLastError(); return false; }
+    const int ppw = 32 / lanes;
+    g.n_tasks = (g.n_pairs + ppw - 1) / ppw;
+    const int64_t tasks_blocks = (g.n_tasks * 32 + g.threads - 1) / g.threads;
+    g.blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)n_sm * bps, tasks_blocks));
+    // two survivor buffers per resident warp: one being written, one being traced back
+    g.surv_bytes = 2u * (size_t)g.blocks * g.threads * (size_t)g.wpad_cap * g.geom.NW * 4u;
+    return true;
+}
+
+vd_status launch_group(const vd_batch_group &g, const int8_t *llr_user, const int8_t *llr_int, uint32_t *out,
+                       int *counter, int *status, cudaStream_t cs) {
+    vd::BatchParams p;
+    p.pk = g.d_pk;
+    p.pairs = g.d_pairs;
+    p.n_pairs = g.n_pairs;
+    p.n_tasks = g.n_tasks;
+    p.llr_user = llr_user;
+    p.llr_int = llr_int;
+    p.out = out;
+    p.counter = counter;
+    p.surv = g.d_surv;
+    p.wpad_cap = g.wpad_cap;
+    p.status = status;
+    const cudaError_t e = g.kind == vd::KIND_K7_R2 ? vd::launch_batch_k7(g.lanes, g.r4, p, g.blocks, cs)
+                                                   : vd::launch_batch_k9(g.lanes, g.r4, p, g.blocks, cs);
+    return e == cudaSuccess ? VD_OK : cuda_fail(e, "batch launch");
+}
+
+// Measured choice of radix and lanes per code kind: every candidate shape
+// runs the plan's own work list twice on zero LLRs (the kernels' control flow
+// and memory traffic do not depend on the values), and the fastest stays.
+vd_status autotune_shapes(vd_batch_plan *pl, const vd_code *const *codes, const vd_packet *packets,
+                          int64_t n_packets, bool tune_radix, bool tune_lanes, int n_sm, cudaStream_t cs) {
+    int64_t user_bytes = 16, out_words = 1;
+    for (int64_t i = 0; i < n_packets; ++i) {
+        const vd_packet &p = packets[i];
+        const vd_code *c = codes[p.code_id];
+        const int64_t T = p.n_info + ((p.flags & VD_TERMINATED) ? c->K - 1 : 0);
+        if (!c->punctured && p.llr_type == VD_LLR_S8) user_bytes = std::max(user_bytes, p.llr_offset + T * c->beta);
+        out_words = std::max(out_words, p.out_word_offset + (p.n_info + 31) / 32);
+    }
+    int8_t *d_user = nullptr;
+    uint32_t *d_out = nullptr;
+    uint32_t *d_surv = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    vd_status st = VD_OK;
+    auto cleanup = [&] {
+        cudaFree(d_user);
+        cudaFree(d_out);
+        cudaFree(d_surv);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc((void **)&d_user, (size_t)user_bytes) != cudaSuccess ||
+        cudaMalloc((void **)&d_out, (size_t)out_words * 4u) != cudaSuccess ||
+        cudaMemsetAsync(d_user, 0, (size_t)user_bytes, cs) != cudaSuccess ||
+        (pl->d_llr_int && cudaMemsetAsync(pl->d_llr_int, 0, pl->llr_int_bytes, cs) != cudaSuccess) ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(VD_ENOMEM, "cannot allocate the autotuner's scratch");
+    }
+    size_t surv_cap = 0;
+    for (size_t gi = 0; gi < pl->groups.size(); ++gi) {
+        vd_batch_group &g = pl->groups[gi];
+        struct Shape { int lanes; bool r4; };
+        std::vector<Shape> cands;
+        const int lane_opts[2] = {g.kind == vd::KIND_K7_R2 ? 1 : 4, g.kind == vd::KIND_K7_R2 ? 2 : 8};
+        for (int L : lane_opts)
+            for (bool r4 : {false, true})
+                if ((tune_lanes || L == g.lanes) && (tune_radix || r4 == g.r4)) cands.push_back({L, r4});
+        float best_ms = 1e30f;
+        Shape best = {g.lanes, g.r4};
+        for (const Shape &sh : cands) {
+            vd_batch_group c = g;
+            if (!shape_group(c, sh.lanes, sh.r4, n_sm)) continue;
+            if (c.surv_bytes > surv_cap) {
+                cudaFree(d_surv);
+                d_surv = nullptr;
+                if (cudaMalloc((void **)&d_surv, c.surv_bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    surv_cap = 0;
+                    continue;   // this shape does not fit in memory now: skip it
+                }
+                surv_cap = c.surv_bytes;
+            }
+            c.d_surv = d_surv;
+            int *counter = pl->d_counters + 16 * (int)gi;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && st == VD_OK; ++rep) {
+                if (rep == 1 && cudaEventRecord(e0, cs) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+                if (cudaMemsetAsync(counter, 0, sizeof(int), cs) != cudaSuccess)
+                    st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+                if (st == VD_OK) st = launch_group(c, d_user, pl->d_llr_int, d_out, counter, pl->d_status, cs);
+            }
+            if (st == VD_OK && cudaEventRecord(e1, cs) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+            if (st == VD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
+            if (st != VD_OK) { cleanup(); return st; }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = sh; }
+        }
+        if (best.lanes != g.lanes || best.r4 != g.r4) {
+            cudaFree(g.d_surv);
+            g.d_surv = nullptr;
+            if (!shape_group(g, best.lanes, best.r4, n_sm) ||
+                cudaMalloc((void **)&g.d_surv, g.surv_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                cleanup();
+                return fail(VD_ENOMEM, "cannot allocate %zu bytes of survivor scratch", g.surv_bytes);
+            }
+        }
+    }
+    cleanup();
+    // the tuning launches leave no trace: clear the status word
+    if (cudaMemsetAsync(pl->d_status, 0, 64 * sizeof(int), cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "autotuner clean-up");
+    return VD_OK;
+}
+
 }  // namespace
 
 extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *const *codes, int n_codes,
@@ -231,6 +362,7 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
         if (c->punctured || p.llr_type == VD_LLR_S4) {
             const int64_t T = p.n_info + ((p.flags & VD_TERMINATED) ? c->K - 1 : 0);
             PrepJob j;
+            j.src = nullptr;
             j.src_off = p.llr_offset;
             j.dst_off = int_bytes;
             j.T = T;
@@ -340,12 +472,8 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
         }
         pl->frames += (int64_t)frs.size();
         g.n_pairs = (int64_t)pairs.size();
-        g.n_tasks = (g.n_pairs + ppw - 1) / ppw;
         g.wpad_cap = frs.empty() ? U : (int32_t)frs.front().wpad;
-        const int64_t tasks_blocks = (g.n_tasks * 32 + g.threads - 1) / g.threads;
-        g.blocks = std::max<int64_t>(1, std::min(g.blocks, tasks_blocks));
-        // two survivor buffers per resident warp: one being written, one being traced back
-        g.surv_bytes = 2u * (size_t)g.blocks * g.threads * (size_t)g.wpad_cap * g.geom.NW * 4u;
+        if (!shape_group(g, g.lanes, g.r4, n_sm)) { free_plan(pl); return fail(VD_ECUDA, "occupancy query"); }
         if ((st = upload(&g.d_pk, pds, cs)) != VD_OK || (st = upload(&g.d_pairs, pairs, cs)) != VD_OK) {
             pl->groups.push_back(g);
             free_plan(pl);
@@ -377,6 +505,12 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
     if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan counters"); }
     e = cudaStreamSynchronize(cs);   // host vectors above go out of scope
     if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "cudaStreamSynchronize"); }
+    const bool tune_radix = !tune || tune->radix == 0, tune_lanes = !tune || tune->lanes == 0;
+    if ((tune_radix || tune_lanes) && (st = autotune_shapes(pl, codes, packets, n_packets, tune_radix,
+                                                            tune_lanes, n_sm, cs)) != VD_OK) {
+        free_plan(pl);
+        return st;
+    }
     *out = pl;
     return VD_OK;
 }
@@ -407,21 +541,10 @@ extern "C" vd_status vd_batch_plan_launch(vd_batch_plan *pl, const void *d_llr_a
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     int gi = 0;
     for (auto &g : pl->groups) {
-        vd::BatchParams p;
-        p.pk = g.d_pk;
-        p.pairs = g.d_pairs;
-        p.n_pairs = g.n_pairs;
-        p.n_tasks = g.n_tasks;
-        p.llr_user = (const int8_t *)d_llr_arena;
-        p.llr_int = pl->d_llr_int;
-        p.out = d_out_arena;
-        p.counter = pl->d_counters + 16 * gi;   // separate cache lines per group
-        p.surv = g.d_surv;
-        p.wpad_cap = g.wpad_cap;
-        p.status = pl->d_status;
-        e = g.kind == vd::KIND_K7_R2 ? vd::launch_batch_k7(g.lanes, g.r4, p, g.blocks, cs)
-                                     : vd::launch_batch_k9(g.lanes, g.r4, p, g.blocks, cs);
-        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+        // separate cache lines per group for the task counters
+        const vd_status st = launch_group(g, (const int8_t *)d_llr_arena, pl->d_llr_int, d_out_arena,
+                                          pl->d_counters + 16 * gi, pl->d_status, cs);
+        if (st != VD_OK) return st;
         ++gi;
         if (gi >= 4) break;
     }

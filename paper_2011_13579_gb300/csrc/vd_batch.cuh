@@ -14,11 +14,13 @@ struct PacketDesc {
     int64_t out_word_off;   // word offset of the packet's decoded bits
     int64_t n_info;
     int32_t f, v;
-    uint32_t flags;         // VD_TERMINATED / VD_START_UNKNOWN; bit 31: LLRs in the internal arena
+    uint32_t flags;         // VD_TERMINATED / VD_START_UNKNOWN; bit 31: LLRs in the internal arena;
+                            // bit 30: llr_off is an absolute device address
     int32_t reserved;
 };
 
 constexpr uint32_t PKT_INTERNAL_LLR = 0x80000000u;
+constexpr uint32_t PKT_ABS_LLR = 0x40000000u;   // llr_off is a device address (caller-owned LLRs)
 
 // One frame pair: packet and frame index of each half (packet ~0u: no frame).
 struct PairRef {
@@ -46,10 +48,11 @@ __device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t
         return t;
     }
     const PacketDesc d = p.pk[pk];
-    const uint32_t fl = d.flags & ~PKT_INTERNAL_LLR;
+    const uint32_t fl = d.flags & ~(PKT_INTERNAL_LLR | PKT_ABS_LLR);
     const int64_t T = d.n_info + ((fl & 1u) ? K - 1 : 0);
     const int64_t n_win = (d.n_info + d.f - 1) / d.f;
-    const int8_t *llr = ((d.flags & PKT_INTERNAL_LLR) ? p.llr_int : p.llr_user) + d.llr_off;
+    const int8_t *llr = (d.flags & PKT_ABS_LLR) ? reinterpret_cast<const int8_t *>(d.llr_off)
+                        : ((d.flags & PKT_INTERNAL_LLR) ? p.llr_int : p.llr_user) + d.llr_off;
     return frame_task(llr, p.out + d.out_word_off, nullptr, (int64_t)s, n_win, d.n_info, T, d.f, d.v, fl);
 }
 
@@ -63,7 +66,12 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     constexpr int NW = Cfg::NW;
     using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW>;
-    __shared__ TbState tbs[NT];
+    // Two traceback records per thread when they fit the static shared
+    // memory: the forward pass writes the next pair's record in place while
+    // the hook walks the previous one, so neither occupies registers.
+    constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
+    constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
+    __shared__ TbState tbs[NREC][NT];
     __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int wlane = (int)(threadIdx.x & 31u);
     const int group = wlane / L;
@@ -74,9 +82,9 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     const size_t buf_words = (size_t)p.wpad_cap * 32u * (size_t)NW;
     uint32_t *surv = p.surv + (size_t)gwarp * 2u * buf_words;
     uint32_t *my_stg = stg[threadIdx.x >> 5];
-    TbState &pend = tbs[threadIdx.x];
-    pend.t0 = -1;
-    pend.tau_store = 0;
+    int cur = 0;   // record of the pair being traced back
+    tbs[0][threadIdx.x].t0 = -1;
+    tbs[0][threadIdx.x].tau_store = 0;
     int buf = 0;
     while (true) {
         int t = 0;
@@ -93,17 +101,28 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
             ft[0] = packet_frame<K>(p, 0xFFFFFFFFu, 0);
             ft[1] = ft[0];
         }
-        TbState tb;
-        forward_pair<K, BETA, GENS, L, RADIX4>(
-            ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, tb,
-            [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
-        Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
-        pend = tb;
-        if (Tb::active(pend)) Tb::begin(pend, my_stg, wlane);
+        TbState &pend = tbs[cur][threadIdx.x];
+        if constexpr (NREC == 2) {
+            TbState &next = tbs[cur ^ 1][threadIdx.x];
+            forward_pair<K, BETA, GENS, L, RADIX4>(
+                ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, next,
+                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+            Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+            cur ^= 1;
+        } else {
+            TbState tb;
+            forward_pair<K, BETA, GENS, L, RADIX4>(
+                ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, tb,
+                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+            Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+            pend = tb;
+        }
+        TbState &now = tbs[cur][threadIdx.x];
+        if (Tb::active(now)) Tb::begin(now, my_stg, wlane);
         buf ^= 1;
         __syncwarp();
     }
-    Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+    Tb::drain(tbs[cur][threadIdx.x], my_stg, wlane, lane, gmask, grp_base);
 }
 
 }  // namespace vd

@@ -32,7 +32,8 @@ struct PrepCode {
 };
 
 struct PrepJob {
-    int64_t src_off;     // first kept value of the packet in the source arena (values)
+    const uint8_t *src;  // NULL: the launch's source arena; else the packet's own values (device)
+    int64_t src_off;     // first kept value of the packet in the source (values)
     int64_t dst_off;     // byte offset of the packet's [T][beta] int8 in the destination
     int64_t T;
     int32_t code_slot;

@@ -58,7 +58,8 @@ struct Req {
     int64_t n_info, T;
     uint32_t flags;
     int32_t f, v;
-    std::vector<uint8_t> llr;      // received values as submitted
+    std::vector<uint8_t> llr;      // received values as submitted (host packets)
+    const uint8_t *dev_llr;        // device packets: the caller's values, read in place
     size_t in_bytes, prep_bytes, out_words;
     int64_t submit_ns, admit_ns, done_ns;
     size_t in_off, prep_off, out_off;   // arena offsets (relative to the batch region)
@@ -207,7 +208,8 @@ bool launch_batch(vd_server *s, Slot &sl) {
     for (Req *r : sl.reqs) {
         if (!r->prep_bytes) continue;
         vd::PrepJob &j = sl.h_jobs[n_jobs++];
-        j.src_off = r->llr_type == VD_LLR_S4 ? (int64_t)(r->in_off * 2) : (int64_t)r->in_off;
+        j.src = r->dev_llr;   // NULL for host packets: their values are in the region
+        j.src_off = r->dev_llr ? 0 : r->llr_type == VD_LLR_S4 ? (int64_t)(r->in_off * 2) : (int64_t)r->in_off;
         j.dst_off = (int64_t)r->prep_off;
         j.T = r->T;
         j.code_slot = r->code_id;
@@ -238,25 +240,41 @@ bool launch_batch(vd_server *s, Slot &sl) {
             Req *r = sl.reqs[members[m]];
             vd::PacketDesc &d = sl.h_pk[ki][m];
             memset(&d, 0, sizeof d);
-            d.llr_off = (int64_t)(r->prep_bytes ? r->prep_off : r->in_off);
             d.out_word_off = (int64_t)(r->out_off / 4);
             d.n_info = r->n_info;
             d.f = r->f;
             d.v = r->v;
-            d.flags = r->flags;   // LLRs are in the arena: "user" arena of this launch
+            if (r->dev_llr && !r->prep_bytes) {
+                // unpunctured int8 device packet: decoded straight from the caller's buffer
+                d.llr_off = (int64_t)(uintptr_t)r->dev_llr;
+                d.flags = r->flags | vd::PKT_ABS_LLR;
+            } else {
+                d.llr_off = (int64_t)(r->prep_bytes ? r->prep_off : r->in_off);
+                d.flags = r->flags;   // LLRs are in the arena: "user" arena of this launch
+            }
             const int64_t nw = (r->n_info + r->f - 1) / r->f;
             for (int64_t f = 0; f < nw; ++f) {
                 const int64_t W = frame_len_of(f, r->n_info, r->T, r->f, r->v);
                 frs.push_back({((W + U - 1) / U) * U, m, (uint32_t)f});
             }
         }
-        std::stable_sort(frs.begin(), frs.end(), [](const Fr &a, const Fr &b) { return a.wpad > b.wpad; });
+        // longest first, stable: a counting sort over the padded lengths
+        // (multiples of U up to wpad_cap), linear in the number of frames
+        const int nb = kr.wpad_cap / U + 1;
+        auto bucket = [&](const Fr &x) {   // a longer frame (never built) goes first; the kernel refuses it
+            return (size_t)std::max<int64_t>(0, nb - 1 - x.wpad / U);
+        };
+        std::vector<int64_t> start((size_t)nb + 1, 0);
+        for (const Fr &x : frs) ++start[bucket(x) + 1];
+        for (int b = 0; b < nb; ++b) start[(size_t)b + 1] += start[(size_t)b];
+        std::vector<Fr> sorted(frs.size());
+        for (const Fr &x : frs) sorted[(size_t)start[bucket(x)]++] = x;
         int64_t np = 0;
-        for (size_t k = 0; k < frs.size(); k += 2) {
+        for (size_t k = 0; k < sorted.size(); k += 2) {
             vd::PairRef &pr = sl.h_pairs[ki][np++];
-            pr.p0 = frs[k].pk;
-            pr.s0 = frs[k].s;
-            if (k + 1 < frs.size()) { pr.p1 = frs[k + 1].pk; pr.s1 = frs[k + 1].s; }
+            pr.p0 = sorted[k].pk;
+            pr.s0 = sorted[k].s;
+            if (k + 1 < sorted.size()) { pr.p1 = sorted[k + 1].pk; pr.s1 = sorted[k + 1].s; }
             else { pr.p1 = 0xFFFFFFFFu; pr.s1 = 0; }
         }
         if (cudaMemcpyAsync(kr.d_pk, sl.h_pk[ki], members.size() * sizeof(vd::PacketDesc),
@@ -360,7 +378,8 @@ void worker_main(vd_server *s) {
                     for (Req *r : batch) { r->in_off = cur; cur += align_up(r->in_bytes); r->admit_ns = t; }
                     for (Req *r : batch) { r->prep_off = cur; cur += align_up(r->prep_bytes); }
                     for (Req *r : batch) { r->out_off = cur; cur += align_up(r->out_words * 4); }
-                    for (Req *r : batch) memcpy(s->h_arena + off + r->in_off, r->llr.data(), r->in_bytes);
+                    for (Req *r : batch)
+                        if (r->in_bytes) memcpy(s->h_arena + off + r->in_off, r->llr.data(), r->in_bytes);
                     free_slot->reqs = batch;
                     free_slot->region_off = off;
                     free_slot->region_bytes = region;
@@ -475,8 +494,10 @@ extern "C" vd_status vd_server_create(vd_server **out, const vd_code *const *cod
     return VD_OK;
 }
 
-extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, const void *host_llr,
-                                      int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
+namespace {
+
+vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr, bool device,
+                        int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
     if (!s) return fail(VD_EINVAL, "server is NULL");
     if (code_id < 0 || code_id >= (int)s->codes.size()) return fail(VD_EINVAL, "bad code_id");
     if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4) return fail(VD_EUNSUPPORTED, "server takes int8 or 4-bit LLRs");
@@ -486,7 +507,7 @@ extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, c
     const int64_t T = n_info + ((flags & VD_TERMINATED) ? c->K - 1 : 0);
     const int64_t kept = vd_num_kept(c, T);
     if (n_values != kept) return fail(VD_EINVAL, "packet has %lld values, the code sends %lld", (long long)n_values, (long long)kept);
-    if (!host_llr) return fail(VD_EINVAL, "host_llr is NULL");
+    if (!llr) return fail(VD_EINVAL, "the LLR pointer is NULL");
     Req *r = new (std::nothrow) Req();
     if (!r) return fail(VD_ENOMEM, "out of host memory");
     r->tag = tag;
@@ -499,10 +520,17 @@ extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, c
     const int32_t F = k7 ? (s->cfg.f7 > 0 ? s->cfg.f7 : 256) : (s->cfg.f9 > 0 ? s->cfg.f9 : 512);
     r->f = n_info <= F ? (int32_t)n_info : F;
     r->v = k7 ? (s->cfg.v7 > 0 ? s->cfg.v7 : 42) : (s->cfg.v9 > 0 ? s->cfg.v9 : 64);
-    r->in_bytes = llr_type == VD_LLR_S4 ? (size_t)((kept + 1) / 2) : (size_t)kept;
+    const size_t value_bytes = llr_type == VD_LLR_S4 ? (size_t)((kept + 1) / 2) : (size_t)kept;
     r->prep_bytes = (c->punctured || llr_type == VD_LLR_S4) ? (size_t)(T * c->beta) : 0;
     r->out_words = (size_t)((n_info + 31) / 32);
-    r->llr.assign((const uint8_t *)host_llr, (const uint8_t *)host_llr + r->in_bytes);
+    if (device) {
+        r->dev_llr = (const uint8_t *)llr;
+        r->in_bytes = 0;   // nothing to upload: read in place on the device
+    } else {
+        r->dev_llr = nullptr;
+        r->in_bytes = value_bytes;
+        r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + r->in_bytes);
+    }
     r->submit_ns = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -513,6 +541,18 @@ extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, c
     }
     s->cv.notify_all();
     return VD_OK;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, const void *host_llr,
+                                      int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
+    return submit_common(s, code_id, llr_type, host_llr, false, n_values, n_info, flags, tag);
+}
+
+extern "C" vd_status vd_server_submit_device(vd_server *s, int code_id, int llr_type, const void *d_llr,
+                                             int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
+    return submit_common(s, code_id, llr_type, d_llr, true, n_values, n_info, flags, tag);
 }
 
 extern "C" int64_t vd_server_poll(vd_server *s, vd_completion *comp, int64_t max_completions,
@@ -563,11 +603,13 @@ extern "C" void vd_server_destroy(vd_server *s) {
     free_server(s);
 }
 
-extern "C" vd_status vd_server_replay(vd_server *s, int64_t n, const int32_t *code_id, const int32_t *llr_type,
-                                      const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
-                                      const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
-                                      int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
-                                      const int64_t *word_offset, int64_t *span_ns) {
+namespace {
+
+vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                      const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                      const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
+                      int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
+                      const int64_t *word_offset, int64_t *span_ns) {
     if (!s) return fail(VD_EINVAL, "server is NULL");
     if (n < 0) return fail(VD_EINVAL, "n < 0");
     if (n > 0 && (!code_id || !llr_type || !host_llr || !llr_offset || !n_values || !n_info || !flags ||
@@ -598,8 +640,8 @@ extern "C" vd_status vd_server_replay(vd_server *s, int64_t n, const int32_t *co
                         (long long)n, (long long)timeout_ms);
         }
         while (next < n && arrival_ns[next] <= now - t0) {
-            const vd_status st = vd_server_submit(s, code_id[next], llr_type[next], base + llr_offset[next],
-                                                  n_values[next], n_info[next], flags[next], (uint64_t)next);
+            const vd_status st = submit_common(s, code_id[next], llr_type[next], base + llr_offset[next], device,
+                                               n_values[next], n_info[next], flags[next], (uint64_t)next);
             if (st != VD_OK) return st;
             ++next;
         }
@@ -624,4 +666,24 @@ extern "C" vd_status vd_server_replay(vd_server *s, int64_t n, const int32_t *co
     }
     if (span_ns) *span_ns = n ? last_done - first_submit : 0;
     return VD_OK;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_server_replay(vd_server *s, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                                      const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                                      const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
+                                      int64_t timeout_ms, int64_t *latency_ns, uint32_t *words,
+                                      const int64_t *word_offset, int64_t *span_ns) {
+    return replay_core(s, false, n, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, arrival_ns,
+                       timeout_ms, latency_ns, words, word_offset, span_ns);
+}
+
+extern "C" vd_status vd_server_replay_device(vd_server *s, int64_t n, const int32_t *code_id,
+                                             const int32_t *llr_type, const void *d_llr, const int64_t *llr_offset,
+                                             const int64_t *n_values, const int64_t *n_info, const uint32_t *flags,
+                                             const int64_t *arrival_ns, int64_t timeout_ms, int64_t *latency_ns,
+                                             uint32_t *words, const int64_t *word_offset, int64_t *span_ns) {
+    return replay_core(s, true, n, code_id, llr_type, d_llr, llr_offset, n_values, n_info, flags, arrival_ns,
+                       timeout_ms, latency_ns, words, word_offset, span_ns);
 }

@@ -403,8 +403,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     constexpr int NW = Cfg::NW, WPF = Cfg::WPF, NACC = Cfg::NACC;
     constexpr uint32_t LV = C::lv(), MV = C::mv();
     constexpr uint32_t F2 = (uint32_t)Cfg::F * 0x00010001u;
-    constexpr uint32_t SEED0 = (uint32_t)(Cfg::F + C::S) * 0x00010001u;  // state 0 after a reset
-    constexpr uint32_t SEEDX = (uint32_t)Cfg::F * 0x00010001u;           // other states after a reset
+    constexpr uint32_t SEED0 = (uint32_t)(Cfg::F + C::S) * 0x00010001u;  // all-equal start, normalised state 0
 
     // ---------------------------------------------------------- frame plan
     int64_t fa[2], fb[2], fo[2], fe[2];
@@ -436,6 +435,21 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const int tau_store = tauo[0] < tauo[1] ? tauo[0] : tauo[1];
     const int reset_at0 = known[0] ? tau0[0] : -1;
     const int reset_at1 = known[1] ? tau0[1] : -1;
+
+    // the traceback's fixed parameters are written now (tb may live in
+    // shared memory), so they hold no registers during the forward pass
+    tb.out[0] = ft[0].out;
+    tb.out[1] = ft[1].out;
+    tb.surv = surv + (size_t)wlane * NW;
+    tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.onb[0] = tb.onb[1] = 0;
+    tb.tau_store = tau_store;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        tb.tauo[h] = tauo[h];
+        tb.taue[h] = taue[h];
+        tb.toff[h] = (int32_t)(fa[h] - tau0[h]);
+    }
 
     // lane part of the branch output per phase, folded into LLR signs
     uint32_t cbits = 0;
@@ -505,16 +519,17 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             constexpr int PH = S % NB;
             const int tau = c * U + S;
 
-            // re-seed a frame that starts from the reset state (state 0 is
-            // register 0 at every stage: ROTR of 0 is 0)
-            if (tau == reset_at0 || tau == reset_at1) {
-                const uint32_t hm = (tau == reset_at0 ? 0x0000FFFFu : 0u) |
-                                    (tau == reset_at1 ? 0xFFFF0000u : 0u);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t val = (r == 0 && lane == 0) ? SEED0 : SEEDX;
-                    P[r] = (P[r] & ~hm) | (val & hm);
-                }
+            // a frame that starts from the reset state gets its head start at
+            // its first stage.  Until then its half of every metric is the
+            // same value F+S (all-equal start, zero-LLR padding stages and
+            // normalisation all keep metrics equal), so adding S to state 0
+            // (register 0 of lane 0 at every stage: ROTR of 0 is 0) gives it
+            // exactly the lead S over every other state, as in the bound of
+            // the metric range.  (Rare: kept as a branch, not predicated.)
+            if (__builtin_expect(tau == reset_at0 || tau == reset_at1, 0)) {
+                const uint32_t hs = (tau == reset_at0 ? (uint32_t)C::S : 0u) |
+                                    (tau == reset_at1 ? (uint32_t)C::S << 16 : 0u);
+                if (lane == 0) P[0] = add_u16x2(P[0], hs);
             }
 
             // ---- branch metrics of this stage (Eq. BM), both frames at once
@@ -779,21 +794,9 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
         }
     }
 
-    tb.out[0] = ft[0].out;
-    tb.out[1] = ft[1].out;
-    tb.surv = surv + (size_t)wlane * NW;
     tb.R[0] = R[0];
     tb.R[1] = R[1];
-    tb.oacc[0] = tb.oacc[1] = 0u;
-    tb.onb[0] = tb.onb[1] = 0;
     tb.t0 = Wpad - 1;
-    tb.tau_store = tau_store;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        tb.tauo[h] = tauo[h];
-        tb.taue[h] = taue[h];
-        tb.toff[h] = (int32_t)(fa[h] - tau0[h]);
-    }
     return true;
 }
 
@@ -820,11 +823,9 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
                            p.n_info, p.T, p.f, p.v, p.flags);
     }
     uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::NW;
-    TbState tb;
-    forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
-                                           tb, [] {});
     TbState &st = tbs[threadIdx.x];
-    st = tb;
+    forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
+                                           st, [] {});
     uint32_t *my_stg = stg[threadIdx.x >> 5];
     if (Tb::active(st)) {
         Tb::begin(st, my_stg, wlane);

@@ -180,3 +180,28 @@ def test_batch_of_whole_streams_matches_stream_decode():
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
     plan.close()
+
+
+def test_autotuned_shape_gives_the_same_bits(k7_codes):
+    """A plan built without a tune measures the candidate kernel shapes and
+    keeps one; its output equals an explicitly shaped plan's bit for bit."""
+    batch = synth.uneven_packets(n_packets=400, index=4, lo=96, hi=5000)
+    pk = packets_of(batch, f=256, v=42)
+    llr = torch.from_numpy(batch.llr_s8.view(np.uint8)).cuda()
+    nw = int(batch.out_word_offset[-1] + (batch.n_info[-1] + 31) // 32)
+    auto = vd.BatchPlan(k7_codes, pk)
+    info = auto.info()
+    assert info.radix in (2, 4) and info.lanes in (1, 2)
+    fixed_tune = vd.VdTune()
+    fixed_tune.radix = 4 if info.radix == 2 else 2
+    fixed_tune.lanes = 2 if info.lanes == 1 else 1
+    fixed = vd.BatchPlan(k7_codes, pk, tune=fixed_tune)
+    out_a = torch.full((nw,), -1, dtype=torch.int32, device="cuda")
+    out_f = torch.full((nw,), -2, dtype=torch.int32, device="cuda")
+    auto.launch(llr, out_a)
+    fixed.launch(llr, out_f)
+    auto.status()
+    fixed.status()
+    assert torch.equal(out_a, out_f)
+    auto.close()
+    fixed.close()

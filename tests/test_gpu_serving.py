@@ -146,3 +146,46 @@ def test_replay_open_loop_matches_alone():
                       fl["n_values"][:1], fl["n_info"][:1], np.full(1, vd.VD_TERMINATED, np.uint32),
                       np.zeros(1, np.int64))
     server.close()
+
+
+def test_device_resident_packets_match_alone():
+    """Packets whose values are already in device memory (read in place, no
+    upload; punctured ones expanded into the arena) decode to the same bits
+    as alone, mixed with host packets and through the device replay."""
+    codes = make_codes()
+    cfg = vd.VdServerConfig()
+    cfg.max_batch = 64
+    server = vd.Server(codes, cfg)
+    pkts = synth.serving_packets(240, index=93)
+    fl = synth.flatten_packets(pkts)
+    dev = torch.from_numpy(fl["llr"].view(np.uint8)).cuda()
+    got = {}
+    for i, p in enumerate(pkts):
+        if i % 3 == 0:
+            server.submit(p.code_id, vd.VD_LLR_S8, p.llr_s8, p.llr_s8.size, p.n_info, vd.VD_TERMINATED, i)
+        else:
+            server.submit_device(p.code_id, vd.VD_LLR_S8, dev.data_ptr() + int(fl["llr_offset"][i]),
+                                 p.llr_s8.size, p.n_info, vd.VD_TERMINATED, i)
+    t_end = time.time() + 60
+    while len(got) < len(pkts) and time.time() < t_end:
+        for c, w in server.poll():
+            assert c.status == vd.VD_OK
+            got[c.tag] = w
+        time.sleep(0.001)
+    assert len(got) == len(pkts)
+    for i in range(0, len(pkts), 3):
+        want, _, _ = alone(codes, pkts[i])
+        assert np.array_equal(got[i], want), i
+    for i in range(1, len(pkts), 3):
+        want, _, _ = alone(codes, pkts[i])
+        assert np.array_equal(got[i], want), i
+    n = len(pkts)
+    arr = synth.poisson_arrivals(np.random.Generator(np.random.PCG64(6)), n, 50000.0)
+    lat, words, span = server.replay(fl["code_id"], np.zeros(n, np.int32), dev, fl["llr_offset"],
+                                     fl["n_values"], fl["n_info"], np.full(n, vd.VD_TERMINATED, np.uint32),
+                                     arr, timeout_ms=60000, word_offset=fl["word_offset"])
+    assert (lat > 0).all() and span > 0
+    for i in range(0, n, 4):
+        o = int(fl["word_offset"][i])
+        assert np.array_equal(words[o:o + got[i].size], got[i]), i
+    server.close()
