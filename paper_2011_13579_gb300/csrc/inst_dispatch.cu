@@ -45,6 +45,21 @@ cudaError_t batch_occupancy_k9(int lanes, bool radix4, int *blocks_per_sm) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_stream_persistent(int K, int lanes, bool radix4, const StreamParams &p, int64_t blocks,
+                                     cudaStream_t st) {
+#define X(KK, R4, L) \
+    if (K == KK && radix4 == R4 && lanes == L) return launch_stream_persistent_v<KK, R4, L>(p, blocks, st);
+    VD_VARIANT_LIST(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+cudaError_t stream_persistent_occupancy(int K, int lanes, bool radix4, int *blocks_per_sm) {
+#define X(KK, R4, L) if (K == KK && radix4 == R4 && lanes == L) return occupancy_stream_v<KK, R4, L>(blocks_per_sm);
+    VD_VARIANT_LIST(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
 bool geom_k7(int lanes, bool radix4, KernelGeom *g) {
 #define X(K, R4, L)                                                        \
     if (K == 7 && radix4 == R4 && lanes == L) {                            \

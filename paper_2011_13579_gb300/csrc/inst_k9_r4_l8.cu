@@ -6,5 +6,7 @@ namespace vd {
 template cudaError_t launch_stream_v<9, true, 8>(const StreamParams &, int64_t, cudaStream_t);
 template cudaError_t launch_batch_v<9, true, 8>(const BatchParams &, int64_t, cudaStream_t);
 template cudaError_t occupancy_v<9, true, 8>(int *);
+template cudaError_t launch_stream_persistent_v<9, true, 8>(const StreamParams &, int64_t, cudaStream_t);
+template cudaError_t occupancy_stream_v<9, true, 8>(int *);
 
 }  // namespace vd

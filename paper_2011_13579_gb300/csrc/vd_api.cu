@@ -138,7 +138,8 @@ struct Scratch {
 };
 
 std::mutex g_scratch_mu;
-// (device, stream, slot) -> buffer; slot 0 = survivors, 1 = depunctured LLRs
+// (device, stream, slot) -> buffer; slot 0 = survivors, 1 = depunctured LLRs,
+// 2 = the status word (stream 0), 3 = the persistent kernel's task counter
 std::map<std::tuple<int, uintptr_t, int>, Scratch> g_scratch;
 
 vd_status get_scratch(int slot, size_t bytes, cudaStream_t st, void **out) {
@@ -299,11 +300,31 @@ bool geometry(vd::CodeKind kind, int lanes, bool r4, vd::KernelGeom *g) {
 struct Plan {
     int lanes;
     bool r4;
+    bool persistent;   // integer LLRs: the persistent kernel with interleaved traceback
     vd::KernelGeom geom;
-    int64_t T, n_win, n_pairs, blocks;
+    int64_t T, n_win, n_pairs, n_tasks, blocks;
     int32_t wpad_max;
     size_t surv_bytes;
 };
+
+// Resident blocks per SM of the persistent stream kernel, per device and shape.
+int persistent_blocks_per_sm(int K, int lanes, bool r4) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, K, lanes, (int)r4);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int bps = 0;
+    if (vd::stream_persistent_occupancy(K, lanes, r4, &bps) != cudaSuccess) {
+        cudaGetLastError();
+        bps = 0;
+    }
+    cache[key] = bps;
+    return bps;
+}
 
 vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, uint32_t flags,
                     const vd_tune *tune, Plan *pl, bool f32 = false) {
@@ -329,8 +350,29 @@ vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, u
     if (wpad > (1 << 30)) return fail(VD_EINVAL, "frame too long (%lld stages)", (long long)wmax);
     pl->wpad_max = (int32_t)wpad;
     const int64_t threads = pl->n_pairs * pl->lanes;
-    pl->blocks = (threads + vd::kThreads - 1) / vd::kThreads;
-    pl->surv_bytes = (size_t)pl->blocks * vd::kThreads * (size_t)wpad * pl->geom.NW * 4u;
+    pl->n_tasks = (pl->n_pairs + 32 / pl->lanes - 1) / (32 / pl->lanes);
+    pl->persistent = false;
+    if (!f32) {
+        // Long streams (at least two tasks per resident warp): resident warps
+        // pull tasks and hide each task's traceback behind the next task's
+        // forward pass; each owns two survivor buffers.  Shorter streams are
+        // one wave of warps, for which the one-pair-per-lane-group kernel is
+        // as fast and needs no task counter.
+        int n_sm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const int bps = persistent_blocks_per_sm(c->K, pl->lanes, pl->r4);
+        const int64_t resident_warps = (int64_t)n_sm * bps * (vd::kThreads / 32);
+        if (bps >= 1 && pl->n_tasks >= 2 * resident_warps) {
+            pl->persistent = true;
+            pl->blocks = (int64_t)n_sm * bps;
+            pl->surv_bytes = 2u * (size_t)pl->blocks * vd::kThreads * (size_t)wpad * pl->geom.NW * 4u;
+        }
+    }
+    if (!pl->persistent) {
+        pl->blocks = (threads + vd::kThreads - 1) / vd::kThreads;
+        pl->surv_bytes = (size_t)pl->blocks * vd::kThreads * (size_t)wpad * pl->geom.NW * 4u;
+    }
     return VD_OK;
 }
 
@@ -424,9 +466,22 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     st = device_status_word(cs, &status);
     if (st != VD_OK) return st;
     p.status = status;
+    p.counter = nullptr;
+    p.n_tasks = pl.n_tasks;
     if (pl.blocks > 0x7FFFFFFF) return fail(VD_EINVAL, "stream too long for one launch");
     cudaError_t e;
     p.llr_bytes = pl.T * c->beta * (f32 ? 2 : 1);
+    if (pl.persistent) {
+        void *ctr = nullptr;
+        st = get_scratch(3, 256, cs, &ctr);
+        if (st != VD_OK) return st;
+        e = cudaMemsetAsync(ctr, 0, sizeof(int), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (task counter)");
+        p.counter = (int *)ctr;
+        e = vd::launch_stream_persistent(c->K, pl.lanes, pl.r4, p, pl.blocks, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+        return VD_OK;
+    }
     switch (c->kind) {
     case vd::KIND_K7_R2:
         e = f32 ? vd::launch_stream_f32_k7(pl.lanes, p, pl.blocks, cs)

@@ -56,12 +56,15 @@ __device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t
     return frame_task(llr, p.out + d.out_word_off, nullptr, (int64_t)s, n_win, d.n_info, T, d.f, d.v, fl);
 }
 
-// Each resident warp loops over tasks.  While it runs the forward procedure of
-// a task, it walks the previous task's traceback one group per chunk (the two
-// tasks' survivors live in the two halves of the warp's scratch), so the
-// traceback's latency hides behind forward work.
-template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
-__global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const BatchParams p) {
+// The persistent decode loop.  Each resident warp pulls tasks of 32/L frame
+// pairs from *counter; pair_of(pair index, ft) gives the two frames of a pair.
+// While it runs the forward procedure of a task, the warp walks the previous
+// task's traceback one group per chunk (the two tasks' survivors live in the
+// two halves of the warp's scratch), so the traceback's latency hides behind
+// forward work.  surv: per resident warp 2 x wpad_cap x 32 x NW words.
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT, typename PairOf>
+__device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks, uint32_t *surv_all,
+                                                  int32_t wpad_cap, int *status, PairOf &&pair_of) {
     constexpr int PPW = 32 / L;
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     constexpr int NW = Cfg::NW;
@@ -69,6 +72,63 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     // Two traceback records per thread when they fit the static shared
     // memory: the forward pass writes the next pair's record in place while
     // the hook walks the previous one, so neither occupies registers.
+    constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
+    constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
+    __shared__ TbState tbs[NREC][NT];
+    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
+    const int wlane = (int)(threadIdx.x & 31u);
+    const int group = wlane / L;
+    const int lane = wlane % L;
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
+    const int grp_base = wlane & ~(L - 1);
+    const int64_t gwarp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const size_t buf_words = (size_t)wpad_cap * 32u * (size_t)NW;
+    uint32_t *surv = surv_all + (size_t)gwarp * 2u * buf_words;
+    uint32_t *my_stg = stg[threadIdx.x >> 5];
+    int cur = 0;   // record of the pair being traced back
+    tbs[0][threadIdx.x].t0 = -1;
+    tbs[0][threadIdx.x].tau_store = 0;
+    int buf = 0;
+    while (true) {
+        int t = 0;
+        if (wlane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (t >= n_tasks) break;
+        FrameTask ft[2];
+        pair_of((int64_t)t * PPW + group, ft);
+        TbState &pend = tbs[cur][threadIdx.x];
+        if constexpr (NREC == 2) {
+            TbState &next = tbs[cur ^ 1][threadIdx.x];
+            forward_pair<K, BETA, GENS, L, RADIX4>(
+                ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, next,
+                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+            Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+            cur ^= 1;
+        } else {
+            TbState tb;
+            forward_pair<K, BETA, GENS, L, RADIX4>(
+                ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, tb,
+                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+            Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
+            pend = tb;
+        }
+        TbState &now = tbs[cur][threadIdx.x];
+        if (Tb::active(now)) Tb::begin(now, my_stg, wlane);
+        buf ^= 1;
+        __syncwarp();
+    }
+    Tb::drain(tbs[cur][threadIdx.x], my_stg, wlane, lane, gmask, grp_base);
+}
+
+// Batches: pairs come from the plan's sorted work list of packet frames.  The
+// loop is spelled out here rather than through persistent_decode: the two
+// forms decode identically, and this one compiles to fewer spills.
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+__global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const BatchParams p) {
+    constexpr int PPW = 32 / L;
+    using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
+    constexpr int NW = Cfg::NW;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW>;
     constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
     constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
     __shared__ TbState tbs[NREC][NT];
@@ -123,6 +183,23 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
         __syncwarp();
     }
     Tb::drain(tbs[cur][threadIdx.x], my_stg, wlane, lane, gmask, grp_base);
+}
+
+// One long stream (vd_decode): pair q is frames 2q and 2q+1 of the stream.
+// counter and n_tasks come in through StreamParams; p.surv holds the
+// persistent warps' double buffers (p.wpad_max stages each).
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+__global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) stream_persistent_kernel(const StreamParams p) {
+    constexpr int NS = 1 << (K - 1);
+    persistent_decode<K, BETA, GENS, L, RADIX4, NT>(
+        p.counter, p.n_tasks, p.surv, p.wpad_max, p.status, [=](int64_t q, FrameTask (&ft)[2]) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t s = 2 * q + h;
+                ft[h] = frame_task(p.llr, p.out, p.pm_out ? p.pm_out + s * NS : nullptr, s, p.n_win, p.n_info,
+                                   p.T, p.f, p.v, p.flags);
+            }
+        });
 }
 
 }  // namespace vd

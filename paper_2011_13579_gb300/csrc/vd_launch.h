@@ -34,6 +34,10 @@ cudaError_t launch_batch_k9(int lanes, bool radix4, const BatchParams &p, int64_
                             cudaStream_t st);
 cudaError_t batch_occupancy_k7(int lanes, bool radix4, int *blocks_per_sm);
 cudaError_t batch_occupancy_k9(int lanes, bool radix4, int *blocks_per_sm);
+// Persistent stream decode (K = 7 or 9): p.counter must be zero at launch.
+cudaError_t launch_stream_persistent(int K, int lanes, bool radix4, const StreamParams &p, int64_t blocks,
+                                     cudaStream_t st);
+cudaError_t stream_persistent_occupancy(int K, int lanes, bool radix4, int *blocks_per_sm);
 cudaError_t launch_stream_f32_k7(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st);
 cudaError_t launch_stream_f32_k9(int lanes, const StreamParams &p, int64_t blocks, cudaStream_t st);
 bool geom_f32_k7(int lanes, KernelGeom *g);

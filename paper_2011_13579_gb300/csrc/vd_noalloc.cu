@@ -138,6 +138,8 @@ extern "C" vd_status vd_decode_noalloc(const vd_code *c, const void *d_llr, int6
     p.surv = (uint32_t *)scratch;
     p.pm_out = nullptr;
     p.status = status;
+    p.counter = nullptr;   // the non-persistent kernel takes no task counter
+    p.n_tasks = 0;
     e = (c->kind == vd::KIND_K7_R2) ? vd::launch_stream_k7(lanes, radix == 4, p, blocks, cs)
                                     : vd::launch_stream_k9(lanes, radix == 4, p, blocks, cs);
     if (e != cudaSuccess) return fail(VD_ECUDA, "decode launch: %s", cudaGetErrorString(e));

@@ -52,6 +52,8 @@ struct StreamParams {
     uint32_t *surv;         // survivor scratch: wpad_max x 32 x NW words per warp
     int32_t *pm_out;        // optional [n_win][2^(K-1)] canonical final metrics
     int *status;            // device status word (bit 0: a frame pair exceeded the scratch)
+    int *counter;           // persistent form: task counter, zero at launch
+    int64_t n_tasks;        // persistent form: tasks of 32/L frame pairs
 };
 
 // One frame as the decoder core sees it: stage indices are relative to the
