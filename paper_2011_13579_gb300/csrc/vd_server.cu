@@ -59,7 +59,9 @@ struct Req {
     uint32_t flags;
     int32_t f, v;
     std::vector<uint8_t> llr;      // received values as submitted (host packets)
-    const uint8_t *dev_llr;        // device packets: the caller's values, read in place
+    const uint8_t *dev_llr;        // values the kernels read in place: the caller's device buffer, or
+                                   // the packet's copy in the pinned staging area (mapped)
+    size_t stage_off, stage_bytes; // the packet's staging region (stage_bytes 0: none)
     size_t in_bytes, prep_bytes, out_words;
     int64_t submit_ns, admit_ns, done_ns;
     size_t in_off, prep_off, out_off;   // arena offsets (relative to the batch region)
@@ -141,6 +143,12 @@ struct vd_server {
     int device = 0, n_sm = 0;
     uint8_t *d_arena = nullptr, *h_arena = nullptr;
     Arena arena;
+    // pinned, device-mapped staging for host packets: submit copies the
+    // values there once and the kernels read them over the host link, so
+    // the worker neither copies them again nor uploads them
+    uint8_t *h_stage = nullptr, *d_stage = nullptr;
+    Arena stage;
+    std::mutex stage_mu;
     std::vector<Slot> slots;
     int *d_status = nullptr;
     int64_t max_pairs = 0;
@@ -181,6 +189,7 @@ void free_server(vd_server *s) {
     }
     cudaFree(s->d_arena);
     cudaFreeHost(s->h_arena);
+    cudaFreeHost(s->h_stage);
     cudaFree(s->d_status);
     for (Req *r : s->pending) delete r;
     for (Req *r : s->done_q) delete r;
@@ -208,7 +217,7 @@ bool launch_batch(vd_server *s, Slot &sl) {
     for (Req *r : sl.reqs) {
         if (!r->prep_bytes) continue;
         vd::PrepJob &j = sl.h_jobs[n_jobs++];
-        j.src = r->dev_llr;   // NULL for host packets: their values are in the region
+        j.src = r->dev_llr;   // NULL: the values came up with the batch, into the region
         j.src_off = r->dev_llr ? 0 : r->llr_type == VD_LLR_S4 ? (int64_t)(r->in_off * 2) : (int64_t)r->in_off;
         j.dst_off = (int64_t)r->prep_off;
         j.T = r->T;
@@ -336,6 +345,11 @@ void worker_main(vd_server *s) {
             }
             if (q != cudaSuccess) s->error.store((int)q);
             s->arena.release(sl.region_off, sl.region_bytes);
+            {
+                std::lock_guard<std::mutex> sk(s->stage_mu);
+                for (Req *r : sl.reqs)
+                    if (r->stage_bytes) s->stage.release(r->stage_off, r->stage_bytes);
+            }
             sl.reqs.clear();
             sl.busy = false;
             did = true;
@@ -443,6 +457,15 @@ extern "C" vd_status vd_server_create(vd_server **out, const vd_code *const *cod
     }
     cudaMemset(s->d_status, 0, 256);
     s->arena.init((size_t)c.device_bytes);
+    // the staging area is optional: without it host packets go through the arena
+    if (cudaHostAlloc((void **)&s->h_stage, (size_t)c.device_bytes, cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer((void **)&s->d_stage, s->h_stage, 0) == cudaSuccess) {
+        s->stage.init((size_t)c.device_bytes);
+    } else {
+        cudaGetLastError();
+        cudaFreeHost(s->h_stage);
+        s->h_stage = s->d_stage = nullptr;
+    }
 
     // which kinds are present, with their frame shape
     bool has[kMaxKinds] = {false, false};
@@ -523,13 +546,28 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
     const size_t value_bytes = llr_type == VD_LLR_S4 ? (size_t)((kept + 1) / 2) : (size_t)kept;
     r->prep_bytes = (c->punctured || llr_type == VD_LLR_S4) ? (size_t)(T * c->beta) : 0;
     r->out_words = (size_t)((n_info + 31) / 32);
+    r->stage_off = r->stage_bytes = 0;
     if (device) {
         r->dev_llr = (const uint8_t *)llr;
         r->in_bytes = 0;   // nothing to upload: read in place on the device
     } else {
-        r->dev_llr = nullptr;
-        r->in_bytes = value_bytes;
-        r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + r->in_bytes);
+        size_t off = 0;
+        bool staged = false;
+        if (s->h_stage) {
+            std::lock_guard<std::mutex> lk(s->stage_mu);
+            staged = s->stage.alloc(align_up(value_bytes), &off);
+        }
+        if (staged) {
+            memcpy(s->h_stage + off, llr, value_bytes);
+            r->dev_llr = s->d_stage + off;
+            r->stage_off = off;
+            r->stage_bytes = align_up(value_bytes);
+            r->in_bytes = 0;
+        } else {   // staging full: the values travel with the batch's upload
+            r->dev_llr = nullptr;
+            r->in_bytes = value_bytes;
+            r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + r->in_bytes);
+        }
     }
     r->submit_ns = now_ns();
     {
