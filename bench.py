@@ -603,8 +603,20 @@ def run_precision(args):
                            "ber": float(np.mean(gh != st.bits)), "ber_delta": float(np.mean(gh != st.bits)) - ber_ref}
         points.append(pt)
         print(json.dumps(pt), file=sys.stderr, flush=True)
+    # roofline of the forms (work = 2 adds + 1 compare-select per state and
+    # stage): the integer forms against 128 lanes x 2 halves per SM and clock,
+    # the fp32 form (one frame per 32-bit lane) against 128 lanes
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(load_peaks().get("sm_max_mhz", 2070.0))
+    opb = ops_per_bit(f, v, 9)
+    peak_int = n_sm * 128 * 2 * mhz * 1e6
+    peak_f32 = n_sm * 128 * mhz * 1e6
+    for pt in points:
+        for form, peak in (("int8", peak_int), ("int4", peak_int), ("fp16_fp32", peak_f32)):
+            pt[form]["roofline_frac"] = pt[form]["gbps"] * 1e9 * opb / peak
     return {"workload": f"K=9 r1/3 (557,663,711), {n} info bits per Eb/N0, f=512, v=64, unterminated",
-            "ber_floor": 100.0 / n, "oracle_threads": threads, "points": points}
+            "ber_floor": 100.0 / n, "oracle_threads": threads, "ops_per_bit": opb,
+            "roofline_peaks_tops": {"int": peak_int / 1e12, "fp32": peak_f32 / 1e12}, "points": points}
 
 
 def kernel_only(args):
@@ -690,7 +702,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": workload_config(2, 0),
+                "config": workload_config(2, 1),
                 "cpu_baseline": {**vals[-1], "value": v},
                 "e2e": {"value": v, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
