@@ -109,7 +109,10 @@ int vd_code_supported(int K, int beta, const uint32_t *gens_octal);
 
 /*
  * Segmented (or full-length) stream decode, Algorithms 1-2 over the frames
- * of Sec. III.
+ * of Sec. III.  Long int8 / 4-bit streams run a persistent kernel whose warps
+ * pull tasks of frame pairs and trace one task back while decoding the next
+ * forward; shorter ones (one wave of warps) a kernel with one frame pair per
+ * lane group.  Both give the same bits.
  *   d_llr:    device pointer to the received LLRs of the whole stream, of
  *             llr_type, in transmitted order (kept positions only when the
  *             code is punctured): n_kept(T) values, T = n_info (+K-1 if
@@ -380,7 +383,10 @@ int64_t vd_num_frames(int64_t n_info, int f);
 /* Number of transmitted LLRs for T stages of this code (puncturing applied). */
 int64_t vd_num_kept(const vd_code *code, int64_t T);
 
-/* Bytes of survivor scratch one stream decode needs (informational). */
+/* Bytes of survivor scratch one stream decode needs (informational, int8
+ * LLRs).  A stream with at least two tasks of frame pairs per resident warp
+ * of the persistent kernel needs a fixed two buffers per resident warp; a
+ * shorter one needs one buffer per frame pair's lane group. */
 int64_t vd_scratch_bytes(const vd_code *code, int64_t n_info, int f, int v, int radix,
                          const vd_tune *tune);
 
