@@ -138,6 +138,15 @@ vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_
                     int f, int v, int radix, uint32_t flags, uint32_t *d_out, int32_t *d_pm,
                     const vd_tune *tune, void *stream);
 
+/*
+ * The configuration vd_decode uses for this code and LLR type when its tune
+ * argument is NULL: f, v and radix as given, and the lanes per frame pair and
+ * threads per block it picks.  The decoded bits depend only on f, v and the
+ * flags, so this is what a reference decoder needs to reproduce a call.
+ * VD_EINVAL on bad arguments, VD_EUNSUPPORTED if there is no kernel.
+ */
+vd_status vd_get_tune(const vd_code *code, int llr_type, int f, int v, int radix, vd_tune *out);
+
 /* ------------------------------------------------------------------ batches
  *
  * Many packets (terminated or not, of up to 16 codes, punctured or not,

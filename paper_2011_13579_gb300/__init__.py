@@ -25,7 +25,7 @@ __all__ = [
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -155,6 +155,8 @@ def lib():
         L.vd_server_replay_device.restype = i32
         L.vd_server_submit_device.argtypes = [vp, i32, i32, vp, i64, i64, u32, ctypes.c_uint64]
         L.vd_server_submit_device.restype = i32
+        L.vd_get_tune.argtypes = [vp, i32, i32, i32, i32, P(VdTune)]
+        L.vd_get_tune.restype = i32
         L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
         L.vd_bm_gate.restype = i32
         L.vd_sync.argtypes = [vp]
@@ -240,6 +242,14 @@ def vd_bm_gate(variant, llr_words, n_pairs, n_stages, checksum, metrics=None, st
                             ctypes.c_void_p(checksum.data_ptr()),
                             ctypes.c_void_p(metrics.data_ptr()) if metrics is not None else None,
                             _stream_handle(stream)))
+
+
+def vd_get_tune(handle, llr_type, f, v, radix) -> "VdTune":
+    """The kernel configuration vd_decode uses with tune=None."""
+    t = VdTune()
+    _check(lib().vd_get_tune(ctypes.c_void_p(handle), int(llr_type), int(f), int(v), int(radix),
+                             ctypes.byref(t)))
+    return t
 
 
 def vd_release_scratch() -> None:

@@ -497,6 +497,25 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     return VD_OK;
 }
 
+extern "C" vd_status vd_get_tune(const vd_code *c, int llr_type, int f, int v, int radix, vd_tune *out) {
+    if (!c || !out) return fail(VD_EINVAL, "NULL argument");
+    if (f <= 0 || v < 0) return fail(VD_EINVAL, "f must be positive and v >= 0");
+    if (radix != 2 && radix != 4) return fail(VD_EINVAL, "radix must be 2 or 4");
+    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16)
+        return fail(VD_EINVAL, "unknown llr_type %d", llr_type);
+    memset(out, 0, sizeof *out);
+    const bool f32 = llr_type == VD_LLR_F16;
+    int lanes = 0;
+    if (f32) lanes = c->kind == vd::KIND_K7_R2 ? 2 : 8;
+    else if (!default_lanes(c->kind, &lanes)) return fail(VD_EUNSUPPORTED, "no kernel for this code");
+    out->f = f;
+    out->v = v;
+    out->radix = f32 ? 2 : radix;   // the fp32 form runs radix-2 steps
+    out->lanes = lanes;
+    out->threads = vd::kThreads;
+    return VD_OK;
+}
+
 extern "C" const char *vd_last_error(void) { return g_err.c_str(); }
 
 void vd_internal_set_error(const char *msg) { g_err = msg; }

@@ -113,3 +113,17 @@ def test_no_cpu_fallback_in_package():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "viterbi_oracle" not in text, fn
+
+
+def test_get_tune_reports_the_decode_configuration():
+    code = vd.Code(7, synth.K7_GENS)
+    t = vd.vd_get_tune(code.handle, vd.VD_LLR_S8, 256, 42, 4)
+    assert (t.f, t.v, t.radix, t.lanes, t.threads) == (256, 42, 4, 1, 128)
+    t = vd.vd_get_tune(code.handle, vd.VD_LLR_F16, 256, 42, 4)
+    assert t.radix == 2 and t.lanes == 2
+    k9 = vd.Code(9, synth.K9_GENS)
+    assert vd.vd_get_tune(k9.handle, vd.VD_LLR_S4, 512, 64, 2).lanes == 4
+    with pytest.raises(vd.VdError):
+        vd.vd_get_tune(code.handle, vd.VD_LLR_S8, 0, 42, 2)
+    with pytest.raises(vd.VdError):
+        vd.vd_get_tune(code.handle, vd.VD_LLR_S8, 256, 42, 3)
