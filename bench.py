@@ -671,7 +671,7 @@ def main():
     ap.add_argument("--precision-bits", type=int, default=1 << 24)
     ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.0, 1.0, 2.0, 3.0, 4.0])
-    ap.add_argument("--e2e-parts", type=int, default=3,
+    ap.add_argument("--e2e-parts", type=int, default=6,
                     help="end-to-end leg: plans the streams are split into so uploads overlap decoding")
     ap.add_argument("--packets", type=int, default=65536,
                     help="packets of the batched-vs-plain comparison (0: skip it)")
