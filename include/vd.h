@@ -83,7 +83,9 @@ typedef struct vd_tune {
     int32_t radix;     /* 2 or 4 */
     int32_t lanes;     /* threads per pair of frames: 1, 2, 4 */
     int32_t threads;   /* threads per block */
-    int32_t reserved[3];
+    int32_t form;      /* vd_decode kernel form: 0 = by stream length, 1 = persistent
+                          (warps pull tasks, interleaved traceback), 2 = one wave */
+    int32_t reserved[2];
 } vd_tune;
 
 /*
@@ -109,10 +111,11 @@ int vd_code_supported(int K, int beta, const uint32_t *gens_octal);
 
 /*
  * Segmented (or full-length) stream decode, Algorithms 1-2 over the frames
- * of Sec. III.  Long int8 / 4-bit streams run a persistent kernel whose warps
- * pull tasks of frame pairs and trace one task back while decoding the next
- * forward; shorter ones (one wave of warps) a kernel with one frame pair per
- * lane group.  Both give the same bits.
+ * of Sec. III.  Long int8 / 4-bit streams (at least one task of frame pairs
+ * per resident warp) run a persistent kernel whose warps pull tasks and trace
+ * one task back while decoding the next forward; shorter ones a kernel with
+ * one frame pair per lane group (tune->form overrides).  Both give the same
+ * bits.
  *   d_llr:    device pointer to the received LLRs of the whole stream, of
  *             llr_type, in transmitted order (kept positions only when the
  *             code is punctured): n_kept(T) values, T = n_info (+K-1 if
@@ -393,7 +396,7 @@ int64_t vd_num_frames(int64_t n_info, int f);
 int64_t vd_num_kept(const vd_code *code, int64_t T);
 
 /* Bytes of survivor scratch one stream decode needs (informational, int8
- * LLRs).  A stream with at least two tasks of frame pairs per resident warp
+ * LLRs).  A stream with at least one task of frame pairs per resident warp
  * of the persistent kernel needs a fixed two buffers per resident warp; a
  * shorter one needs one buffer per frame pair's lane group. */
 int64_t vd_scratch_bytes(const vd_code *code, int64_t n_info, int f, int v, int radix,

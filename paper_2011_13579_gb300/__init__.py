@@ -46,7 +46,7 @@ class VdError(RuntimeError):
 class VdTune(ctypes.Structure):
     _fields_ = [("f", ctypes.c_int32), ("v", ctypes.c_int32), ("radix", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("form", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class VdPacket(ctypes.Structure):

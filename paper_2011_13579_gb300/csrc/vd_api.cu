@@ -307,6 +307,11 @@ struct Plan {
     size_t surv_bytes;
 };
 
+// Streams with at least this many tasks per resident warp take the persistent
+// form (measured on GB300: below one wave the one-pair-per-lane-group kernel
+// is faster, from one wave up the persistent one, for K=7 and K=9).
+constexpr int64_t kPersistentWaves = 1;
+
 // Resident blocks per SM of the persistent stream kernel, per device and shape.
 int persistent_blocks_per_sm(int K, int lanes, bool r4) {
     static std::mutex mu;
@@ -329,6 +334,7 @@ int persistent_blocks_per_sm(int K, int lanes, bool r4) {
 vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, uint32_t flags,
                     const vd_tune *tune, Plan *pl, bool f32 = false) {
     pl->r4 = radix == 4 && !f32;
+    if (tune && (tune->form < 0 || tune->form > 2)) return fail(VD_EINVAL, "tune.form must be 0, 1 or 2");
     if (tune && tune->lanes > 0) {
         pl->lanes = tune->lanes;
     } else if (f32) {
@@ -353,17 +359,18 @@ vd_status make_plan(const vd_code *c, int64_t n_info, int f, int v, int radix, u
     pl->n_tasks = (pl->n_pairs + 32 / pl->lanes - 1) / (32 / pl->lanes);
     pl->persistent = false;
     if (!f32) {
-        // Long streams (at least two tasks per resident warp): resident warps
+        // Long streams (a task per resident warp or more): resident warps
         // pull tasks and hide each task's traceback behind the next task's
         // forward pass; each owns two survivor buffers.  Shorter streams are
-        // one wave of warps, for which the one-pair-per-lane-group kernel is
-        // as fast and needs no task counter.
+        // less than one wave of warps, for which the one-pair-per-lane-group
+        // kernel is faster.
         int n_sm = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         const int bps = persistent_blocks_per_sm(c->K, pl->lanes, pl->r4);
         const int64_t resident_warps = (int64_t)n_sm * bps * (vd::kThreads / 32);
-        if (bps >= 1 && pl->n_tasks >= 2 * resident_warps) {
+        const int form = tune ? tune->form : 0;
+        if (bps >= 1 && (form == 1 || (form == 0 && pl->n_tasks >= kPersistentWaves * resident_warps))) {
             pl->persistent = true;
             pl->blocks = (int64_t)n_sm * bps;
             pl->surv_bytes = 2u * (size_t)pl->blocks * vd::kThreads * (size_t)wpad * pl->geom.NW * 4u;

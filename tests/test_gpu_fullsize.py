@@ -88,8 +88,8 @@ def test_full_packet_batch_sampled_packets_match_oracle():
 
 @pytest.mark.parametrize("radix", [2, 4])
 def test_long_stream_persistent_decode_matches_oracle(radix):
-    """A stream long enough for vd_decode's persistent form (at least two
-    tasks per resident warp): 2^26 + 1000 info bits, K=7, f=256, v=42,
+    """A stream long enough for vd_decode's persistent form (at least one
+    task per resident warp): 2^26 + 1000 info bits, K=7, f=256, v=42,
     terminated — whole stream bit-exact against the oracle."""
     n = (1 << 26) + 1000
     rng = np.random.Generator(np.random.PCG64(2026 + radix))

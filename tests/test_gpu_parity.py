@@ -272,3 +272,32 @@ def test_full_size_segmented_k9_sampled_frames():
         e = min(n, (s + 1) * f)
         assert np.array_equal(gbits[s * f:e], obits[k, :e - s * f]), s
         assert np.array_equal(gpm[s].astype(np.int64), opm[k]), s
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("K,gens,f,v,lanes,kind", [(7, synth.K7_GENS, 256, 42, 1, "s8"),
+                                                   (7, synth.K7_GENS, 128, 30, 2, "s4"),
+                                                   (9, synth.K9_GENS, 512, 64, 4, "s8")])
+def test_both_vd_decode_forms(K, gens, f, v, lanes, kind, form):
+    """vd_decode's persistent form (1) and one-wave form (2), forced through
+    vd_tune.form, give the oracle's bits and canonical metrics, with a
+    terminated ragged end and a pm output."""
+    rng = np.random.Generator(np.random.PCG64(300 + K + form))
+    n = 150_000 + 777
+    st = synth.make_stream(rng, K, gens, n, 2.0, True)
+    q = st.s8() if kind == "s8" else st.s4()
+    kept = q if kind == "s8" else synth.pack_s4(q)
+    code = gpu_code(K, gens)
+    t = vd.VdTune()
+    t.lanes = lanes
+    t.form = form
+    llr = torch.from_numpy(np.ascontiguousarray(kept).view(np.uint8)).cuda()
+    nw = (n + 31) // 32
+    out = torch.zeros(nw, dtype=torch.int32, device="cuda")
+    pm = torch.zeros((vd.vd_num_frames(n, f), 1 << (K - 1)), dtype=torch.int32, device="cuda")
+    vd.vd_decode(code.handle, llr, vd.VD_LLR_S8 if kind == "s8" else vd.VD_LLR_S4, n, f, v, 2,
+                 vd.VD_TERMINATED, out, pm, t)
+    vd.vd_sync()
+    ocode = oracle.Code(K, gens)
+    ow, opm = run_oracle(ocode, full_llr_of(ocode, q, st.T), n, f, v, terminated=True)
+    check(out.cpu().numpy().view(np.uint32), pm.cpu().numpy(), ow, opm, K, n, f, v, st.T, True, False)
