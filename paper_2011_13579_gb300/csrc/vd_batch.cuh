@@ -1,8 +1,9 @@
-// Persistent batched decode: many packets (or streams) of one code kind in
-// one launch.  The host sorts every frame of every packet by length, pairs
-// neighbours, and groups 32/L pairs into a warp task; resident warps pull
-// tasks from a global counter (longest first) and run the same frame-pair
-// forward procedure and traceback as the stream kernel on each.
+// Persistent decode: resident warps pull tasks of 32/L frame pairs from a
+// global counter and run the stream kernel's frame-pair forward procedure on
+// each, while tracing the previous task back.  Batches (many packets of one
+// code kind in one launch): the host sorts every frame of every packet by
+// length and pairs neighbours, longest first.  Long single streams
+// (vd_decode): pair q is frames 2q and 2q+1.
 #pragma once
 #include "vd_stream.cuh"
 

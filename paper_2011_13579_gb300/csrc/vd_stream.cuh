@@ -22,8 +22,8 @@
 //   * frames of a pair are right-aligned on a common padded length Wpad (a
 //     multiple of the unroll period U), so they end together; the shorter
 //     frame is preceded by stages of zero LLRs, which keep all-equal metrics
-//     all-equal, and a frame that starts from the reset state is re-seeded
-//     when its first stage arrives;
+//     all-equal, and a frame that starts from the reset state gets its head
+//     start on state 0 when its first stage arrives;
 //   * decisions go, packed one bit per state and frame, to a global scratch
 //     buffer; a warp's stores for one stage are contiguous.  Bit (r & 31) of
 //     word (r >> 5) holds register r of the lane (r & 15 at bit 16h for a
@@ -34,7 +34,11 @@
 //     and ties), and the survivor of right state j is the 2-bit pair
 //     (d_m, d_i): the decision of j at stage t and the decision of the
 //     middle state it selects at stage t-1, stored at the same bit position
-//     so that one traceback step crosses two stages.
+//     so that one traceback step crosses two stages;
+//   * traceback (Algorithm 2) walks groups of K-1 stages whose survivor words
+//     are staged in shared memory; a group's decoded bits are the register
+//     index at the group's start.  The persistent kernels (vd_batch.cuh) run
+//     one pair's traceback a group per chunk of the next pair's forward pass.
 #pragma once
 #include <utility>
 #include "vd_device.cuh"
