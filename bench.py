@@ -789,6 +789,8 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_oracle_run(args.cpu_seconds)
+            one = cpu_oracle_run(min(5.0, args.cpu_seconds), threads=1)
+            line["cpu_baseline"]["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
         except Exception as exc:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
     print(json.dumps(line), flush=True)
