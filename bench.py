@@ -622,6 +622,36 @@ def run_precision(args):
             "roofline_peaks_tops": {"int": peak_int / 1e12, "fp32": peak_f32 / 1e12}, "points": points}
 
 
+def packets_only(args):
+    """The uneven-packet plan (65,536 packets by default) with a fixed kernel
+    shape (radix 2, one lane: no autotuning launches), W + K CUDA-graph
+    launches and nothing else, for profilers."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+    batch = synth.uneven_packets(args.packets)
+    pats = (None, synth.PUNCT_R23, synth.PUNCT_R34)
+    codes = [vd.Code(K, synth.K7_GENS, puncture=None if p is None else p.tolist()) for p in pats]
+    n = batch.n_packets
+    pk = {"code_id": batch.rate_id.astype(np.int32), "llr_type": np.zeros(n, np.int32),
+          "llr_offset": batch.llr_offset, "n_info": batch.n_info,
+          "flags": np.full(n, vd.VD_TERMINATED, np.uint32), "f": np.zeros(n, np.int32),
+          "v": np.zeros(n, np.int32), "out_word_offset": batch.out_word_offset}
+    tune = vd.VdTune()
+    tune.radix = 2
+    tune.lanes = args.lanes or 1
+    s = torch.cuda.Stream()
+    plan = vd.BatchPlan(codes, pk, tune=tune, stream=s)
+    llr = torch.from_numpy(batch.llr_s8.view(np.uint8)).cuda()
+    nw = int(batch.out_word_offset[-1] + (batch.n_info[-1] + 31) // 32)
+    out = torch.empty(nw, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        plan.launch(llr, out, stream=s, graph=True)
+    torch.cuda.synchronize()
+    plan.close()
+    print(json.dumps({"mode": "packets", "launches": args.warmup + args.steps}))
+
+
 def kernel_only(args):
     """W + K launches and nothing else, for profilers: the batch plan of the six
     2^24-bit streams (--path batch) or one stream's vd_decode (--path stream)."""
@@ -669,8 +699,9 @@ def main():
     ap.add_argument("--serving-pool", type=int, default=8192)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-max-packets", type=int, default=400000)
-    ap.add_argument("--workload", default="stream", choices=["stream", "precision"],
-                    help="precision: the K=9 precision study (int8 / 4-bit / fp16) instead of the bench line")
+    ap.add_argument("--workload", default="stream", choices=["stream", "precision", "packets"],
+                    help="precision: the K=9 precision study (int8 / 4-bit / fp16) instead of the bench line; "
+                         "packets: only W+K graph launches of the uneven-packet plan (for profilers)")
     ap.add_argument("--precision-bits", type=int, default=1 << 24)
     ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.0, 1.0, 2.0, 3.0, 4.0])
@@ -719,6 +750,9 @@ def main():
     if args.workload == "precision":
         if rank == 0:
             print(json.dumps({"precision_study": run_precision(args)}), flush=True)
+        return
+    if args.workload == "packets":
+        packets_only(args)
         return
     if args.mode == "kernel":
         kernel_only(args)
