@@ -14,6 +14,7 @@
 
 #include "../../include/vd.h"
 #include "vd_code.h"
+#include "vd_prep.cuh"
 #include "vd_launch.h"
 
 namespace {
@@ -251,28 +252,12 @@ struct PrepParams {
     int8_t *dst;              // [T][beta]
 };
 
-__device__ __forceinline__ int8_t kept_value(const PrepParams &p, int64_t k) {
-    if (k >= p.n_kept) return 0;
-    if (p.llr_type == VD_LLR_S4) {
-        const uint8_t byte = p.src[k >> 1];
-        const uint8_t nib = (k & 1) ? (byte >> 4) : (byte & 0x0F);
-        return (int8_t)((int8_t)(nib << 4) >> 4);
-    }
-    return (int8_t)p.src[k];
-}
-
 // Expands the transmitted values of each stage to beta int8 LLRs, with 0 at
-// erased positions (depuncturing) and 4-bit values sign-extended.
+// erased positions (depuncturing) and 4-bit values sign-extended
+// (vd_prep.cuh); a grid-stride loop over whole puncturing periods.
 __global__ void prep_kernel(const PrepParams p) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.T) return;
-    const int ph = (int)(t % p.period);
-    int64_t k = (t / p.period) * p.kept_per_period + p.kept_prefix[ph];
-    for (int b = 0; b < p.beta; ++b) {
-        int8_t x = 0;
-        if (p.punct[b][ph]) x = kept_value(p, k++);
-        p.dst[t * p.beta + b] = x;
-    }
+    vd::prep_expand(p.src, 0, p.n_kept, p.llr_type, p.T, p.beta, p.period, p.kept_per_period, p.punct, p.dst,
+                    (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace
@@ -445,7 +430,9 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
         memcpy(pp.kept_prefix, c->kept_prefix, sizeof pp.kept_prefix);
         pp.dst = (int8_t *)buf;
         const int tb = 256;
-        prep_kernel<<<(unsigned)((pl.T + tb - 1) / tb), tb, 0, cs>>>(pp);
+        const int64_t groups = (pl.T + c->period - 1) / c->period;
+        const int64_t blocks = std::min<int64_t>((groups + tb - 1) / tb, 4096);
+        prep_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, cs>>>(pp);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "input pre-pass launch");
         llr = (const int8_t *)buf;

@@ -16,6 +16,7 @@
 #include "../../include/vd.h"
 #include "vd_code.h"
 #include "vd_launch.h"
+#include "vd_prep.cuh"
 
 namespace {
 
@@ -38,31 +39,17 @@ using vd::PrepBatchParams;
 using vd::PrepCode;
 using vd::PrepJob;
 
-__device__ __forceinline__ int8_t batch_kept_value(const uint8_t *src, int64_t k, int llr_type) {
-    if (llr_type == VD_LLR_S4) {
-        const uint8_t byte = src[k >> 1];
-        const uint8_t nib = (k & 1) ? (byte >> 4) : (byte & 0x0F);
-        return (int8_t)((int8_t)(nib << 4) >> 4);
-    }
-    return (int8_t)src[k];
-}
-
 // One block per packet: expand its transmitted values to beta int8 LLRs per
-// stage, 0 at erased positions.
+// stage, 0 at erased positions (vd_prep.cuh).
 __global__ void prep_batch_kernel(const PrepBatchParams p) {
     const int64_t j = blockIdx.x;
     if (j >= p.n_jobs) return;
     const PrepJob jb = p.jobs[j];
     const PrepCode &c = p.codes[jb.code_slot];
-    for (int64_t t = threadIdx.x; t < jb.T; t += blockDim.x) {
-        const int ph = (int)(t % c.period);
-        int64_t k = jb.src_off + (t / c.period) * c.kept_per_period + c.kept_prefix[ph];
-        for (int b = 0; b < c.beta; ++b) {
-            int8_t x = 0;
-            if (c.punct[b][ph]) x = batch_kept_value(jb.src ? jb.src : p.src, k++, jb.llr_type);
-            p.dst[jb.dst_off + t * c.beta + b] = x;
-        }
-    }
+    // the packet's last kept value bounds every read (steps past T read nothing)
+    const int64_t kept_end = jb.src_off + (jb.T / c.period) * c.kept_per_period + c.kept_prefix[jb.T % c.period];
+    vd::prep_expand(jb.src ? jb.src : p.src, jb.src_off, kept_end, jb.llr_type, jb.T, c.beta, c.period,
+                    c.kept_per_period, c.punct, p.dst + jb.dst_off, threadIdx.x, blockDim.x);
 }
 
 // ----------------------------------------------------------------- tuner
