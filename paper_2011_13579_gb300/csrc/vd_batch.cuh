@@ -69,7 +69,7 @@ __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks,
     constexpr int PPW = 32 / L;
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     constexpr int NW = Cfg::NW;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW, Cfg::EMB>;
     // Two traceback records per thread when they fit the static shared
     // memory: the forward pass writes the next pair's record in place while
     // the hook walks the previous one, so neither occupies registers.
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     constexpr int PPW = 32 / L;
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     constexpr int NW = Cfg::NW;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW, Cfg::EMB>;
     constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
     constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
     __shared__ TbState tbs[NREC][NT];

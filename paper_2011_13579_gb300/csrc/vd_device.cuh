@@ -20,6 +20,13 @@
 //     ties included, as Algorithm 1's strict ">" gives) is bit 15 / bit 31 of
 //     the 32-bit sum  c_odd - c_even + 0x8000 (per half), which one 3-input
 //     integer add computes without carries crossing the halves.
+//   * embedded form (radix-2 K=7): a half holds 4 m + j, where the two low
+//     bits j are the decisions of the current stage pair along the state's
+//     survivor.  The odd candidate of stage k of the pair carries + 2^k, so
+//     the max itself sets bit k exactly when the odd predecessor wins or ties
+//     and carries the winner's lower bit along; the fields are stored and
+//     cleared after the pair.  With the scale the bound becomes
+//     4 (F + 2S + (N+1) B) + 3 <= 65535 (unsigned halves), N = 18 for K=7.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

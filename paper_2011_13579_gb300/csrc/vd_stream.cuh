@@ -28,6 +28,11 @@
 //     buffer; a warp's stores for one stage are contiguous.  Bit (r & 31) of
 //     word (r >> 5) holds register r of the lane (r & 15 at bit 16h for a
 //     lane with 16 registers; frame h = 0, 1);
+//   * radix-2 K=7 embeds the decisions in the metrics instead (see
+//     StreamCfg::EMB and forward_pair): each stage pair leaves one record of
+//     2-bit fields per register, word r >> 3 at bits 2 (r & 7) + 16h, whose
+//     bit 1 is the register's decision at the pair's second stage and bit 0
+//     the decision at the first stage of the register that won;
 //   * radix-4: stages are taken in pairs (t-1, t).  The metrics are two
 //     radix-2 steps (grouping the four candidates of a right state by their
 //     middle state, as Eq. radix4:PM allows, gives exactly the same integers
@@ -109,15 +114,26 @@ struct StreamCfg {
     static constexpr int NW = NR >= 32 ? NR / 16 : 1; // survivor words per lane per stage
     static constexpr int WPF = NR >= 32 ? NR / 32 : 1;// survivor words per frame per lane per stage
     static constexpr int NACC = NR >= 16 ? NR / 16 : 1;
+    // Embedded decisions (radix-2, when the range allows): metrics are kept
+    // as 4 m + j, the two low bits j of each half carrying the decisions of
+    // the current stage pair; see forward_pair.  Longest normalisation period
+    // (stages) that keeps 4 (F + 2S + (N+1) B) + 3 within 16 unsigned bits:
+    static constexpr int NMAX_EMB = (16383 - 2 * C::S) / (2 * C::B) - 1;
+    static constexpr bool EMB = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
+    static constexpr int SC = EMB ? 4 : 1;            // metric scale
+    static constexpr int NWE = NR / 8;                // record words per lane per stage pair (EMB)
     // normalisation period (multiple of U), see the header of vd_device.cuh
-    static constexpr int NMAX = (32767 - 2 * C::S) / (2 * C::B) - 1;
+    static constexpr int NMAX = EMB ? NMAX_EMB : (32767 - 2 * C::S) / (2 * C::B) - 1;
     static constexpr int NORM_CHUNKS = (NMAX / U) > 0 ? (NMAX / U) : 1;
     static constexpr int F = (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
     static_assert(NS % L == 0 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
     static_assert(NR >= 2, "at least one butterfly per lane");
     static_assert(!RADIX4 || NB % 2 == 0, "radix-4 pairs need an even rotation period");
     static_assert(NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
-    static_assert(F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767, "metric range");
+    static_assert(EMB ? 4 * (F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B) + 3 <= 65535
+                      : F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767,
+                  "metric range");
+    static_assert(!EMB || NWE * 16 <= 32 * NW, "a stage pair's records fit the per-stage scratch");
 };
 
 template <typename Fn, int... S>
@@ -240,30 +256,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int K, int L, bool RADIX4, int NR, int NW>
+template <int K, int L, bool RADIX4, int NR, int NW, bool EMB = false>
 struct Traceback {
     static constexpr int NB = K - 1;
     static constexpr int G = NB;                 // stages per group
     static constexpr int LR = ilog2(NR);
     static constexpr int WPF = NR >= 32 ? NR / 32 : 1;
-    static constexpr int SLOT_WORDS = G * 32 * NW;
+    // survivor records: one per stage (NW words per lane), or with embedded
+    // decisions one per stage pair (NR / 8 words per lane, 2-bit fields)
+    static constexpr int REC = EMB ? G / 2 : G;  // records per group
+    static constexpr int RW = EMB ? NR / 8 : NW; // words per record and lane
+    static constexpr int SLOT_WORDS = REC * 32 * RW;
     static constexpr int STAGE_WORDS = 2 * SLOT_WORDS;   // per warp
+    static_assert(!EMB || (G % 2 == 0 && !RADIX4), "embedded decisions: radix-2, stage pairs");
 
-    // Copies the words of stages t0, t0-1, .., t0-G+1 (those >= tau_store) to a slot.
+    // Copies the records of stages t0, t0-1, .., t0-G+1 (those >= tau_store) to a slot.
     __device__ static void issue(const TbState &s, int t0, uint32_t *slot, int wlane) {
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int t = t0 - g;
+        for (int g = 0; g < REC; ++g) {
+            const int t = t0 - (EMB ? 2 * g : g);   // EMB: the second stage of a pair
             if (t >= s.tau_store) {
-                uint32_t *dst = slot + (g * 32 + wlane) * NW;
-                const uint32_t *src = s.surv + (size_t)t * 32 * NW;
-                if constexpr (NW == 1) {
+                uint32_t *dst = slot + (g * 32 + wlane) * RW;
+                const uint32_t *src = s.surv + (size_t)(EMB ? (t >> 1) : t) * 32 * RW;
+                if constexpr (RW == 1) {
                     cp_async_bytes4(dst, src);
-                } else if constexpr (NW == 2) {
+                } else if constexpr (RW == 2) {
                     cp_async_bytes8(dst, src);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < NW; i += 4) cp_async_bytes16(dst + i, src + i);
+                    for (int i = 0; i < RW; i += 4) cp_async_bytes16(dst + i, src + i);
                 }
             }
         }
@@ -289,16 +310,16 @@ struct Traceback {
         const int tl = t0 - (G - 1);   // lowest stage of the group
         uint32_t Rh[2] = {s.R[0], s.R[1]};
         const uint32_t Rs[2] = {Rh[0], Rh[1]};
-        auto words = [&](int g, uint32_t (&wd)[NW]) {
-            const uint32_t *p = slot + (g * 32 + wlane) * NW;
-            if constexpr (NW == 1) {
+        auto words = [&](int g, uint32_t (&wd)[RW]) {
+            const uint32_t *p = slot + (g * 32 + wlane) * RW;
+            if constexpr (RW == 1) {
                 wd[0] = p[0];
-            } else if constexpr (NW == 2) {
+            } else if constexpr (RW == 2) {
                 const uint2 x = *reinterpret_cast<const uint2 *>(p);
                 wd[0] = x.x; wd[1] = x.y;
             } else {
 #pragma unroll
-                for (int i = 0; i < NW; i += 4) {
+                for (int i = 0; i < RW; i += 4) {
                     const uint4 x = *reinterpret_cast<const uint4 *>(p + i);
                     wd[i] = x.x; wd[i + 1] = x.y; wd[i + 2] = x.z; wd[i + 3] = x.w;
                 }
@@ -321,7 +342,30 @@ struct Traceback {
             if constexpr (L > 1) return __shfl_sync(gmask, x, grp_base + (int)(R >> LR));
             else return x;
         };
-        if constexpr (!RADIX4) {
+        if constexpr (EMB) {
+            // pair record of stages (t-1, t): register R's 2-bit field holds
+            // the decision of R at stage t (bit 1) and the decision at stage
+            // t-1 of the register it came from (bit 0).  The phases of t and
+            // t-1 are adjacent (t's is odd), so one rotation puts both bits in
+            // place and one select replaces both bits of R.
+            static_for<REC>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                constexpr int ph1 = ((NB - 1 - 2 * j) % NB + NB) % NB;
+                constexpr int ph0 = ph1 - 1;
+                static_assert(ph1 >= 1, "the second stage of a pair has an odd phase");
+                constexpr uint32_t m = 3u << ph0;
+                uint32_t wd[RW];
+                words(j, wd);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t R = Rh[h];
+                    const uint32_t word = RW == 1 ? wd[0] : pick<RW>(wd, (R >> 3) & (uint32_t)(RW - 1));
+                    const uint32_t sh = 2u * (R & 7u) + 16u * (uint32_t)h;
+                    const uint32_t t = owner(__funnelshift_r(word, word, sh - (uint32_t)ph0), R);
+                    Rh[h] = (R & ~m) | (t & m);
+                }
+            });
+        } else if constexpr (!RADIX4) {
             static_for<G>([&](auto gc) {
                 constexpr int g = decltype(gc)::value;
                 constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // group starts at -1 mod (K-1)
@@ -406,10 +450,12 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
     using C = typename Cfg::C;
     constexpr int NB = Cfg::NB, NR = Cfg::NR, LR = Cfg::LR, U = Cfg::U, UW = Cfg::UW;
-    constexpr int NW = Cfg::NW, WPF = Cfg::WPF, NACC = Cfg::NACC;
+    constexpr int NW = Cfg::NW, WPF = Cfg::WPF, NACC = Cfg::NACC, NWE = Cfg::NWE;
+    constexpr bool EMB = Cfg::EMB;
     constexpr uint32_t LV = C::lv(), MV = C::mv();
-    constexpr uint32_t F2 = (uint32_t)Cfg::F * 0x00010001u;
-    constexpr uint32_t SEED0 = (uint32_t)(Cfg::F + C::S) * 0x00010001u;  // all-equal start, normalised state 0
+    constexpr uint32_t F2 = (uint32_t)(Cfg::SC * Cfg::F) * 0x00010001u;
+    constexpr uint32_t S2 = (uint32_t)(Cfg::SC * C::S) * 0x00010001u;
+    constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::F + C::S)) * 0x00010001u;  // all-equal start, normalised state 0
 
     // ---------------------------------------------------------- frame plan
     int64_t fa[2], fb[2], fo[2], fe[2];
@@ -446,7 +492,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     // shared memory), so they hold no registers during the forward pass
     tb.out[0] = ft[0].out;
     tb.out[1] = ft[1].out;
-    tb.surv = surv + (size_t)wlane * NW;
+    tb.surv = surv + (size_t)wlane * (EMB ? NWE : NW);
     tb.oacc[0] = tb.oacc[1] = 0u;
     tb.onb[0] = tb.onb[1] = 0;
     tb.tau_store = tau_store;
@@ -480,6 +526,19 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const int32_t hi0 = valid[0] ? (int32_t)W[0] * BETA : 0, hi1 = valid[1] ? (int32_t)W[1] * BETA : 0;
     int32_t vb0 = -tau0[0] * BETA, vb1 = -tau0[1] * BETA;   // offset of the chunk being fetched
 
+    // EMB: the record of stage pair (tau - 1, tau), stored at pair index tau / 2
+    auto store_rec = [&](int tau, const uint32_t (&rec)[NWE]) {
+        uint32_t *dst = surv + ((size_t)(tau >> 1) * 32 + wlane) * NWE;
+        if constexpr (NWE == 1) {
+            *dst = rec[0];
+        } else if constexpr (NWE == 2) {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(rec[0], rec[1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NWE; i += 4)
+                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(rec[i], rec[i + 1], rec[i + 2], rec[i + 3]);
+        }
+    };
     auto store_words = [&](int tau, const uint32_t (&wd)[NW]) {
         uint32_t *dst = surv + ((size_t)tau * 32 + wlane) * NW;
         if constexpr (NW == 1) {
@@ -496,6 +555,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     // runtime +1 / -1 for the FMA-pipe multiply-adds (blocks are one-dimensional)
     const uint32_t one = threadIdx.y + 1u;
     const uint32_t m1 = 0u - one;
+    const uint32_t four = one << 2;
     constexpr bool COROLLARY = LV == (1u << BETA) - 1u && MV == (1u << BETA) - 1u;
 
     const int nchunks = Wpad / U;
@@ -533,8 +593,8 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             // exactly the lead S over every other state, as in the bound of
             // the metric range.  (Rare: kept as a branch, not predicated.)
             if (__builtin_expect(tau == reset_at0 || tau == reset_at1, 0)) {
-                const uint32_t hs = (tau == reset_at0 ? (uint32_t)C::S : 0u) |
-                                    (tau == reset_at1 ? (uint32_t)C::S << 16 : 0u);
+                const uint32_t hs = (tau == reset_at0 ? (S2 & 0xFFFFu) : 0u) |
+                                    (tau == reset_at1 ? (S2 & 0xFFFF0000u) : 0u);
                 if (lane == 0) P[0] = add_u16x2(P[0], hs);
             }
 
@@ -567,6 +627,73 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     A[x] = add_s16x2(A[x], Lb[b]);
                 }
             }
+            if constexpr (EMB) {
+                // ---- embedded decisions.  A metric half is 4 m + j: m the
+                // path metric (Eq. PM) and j < 4 the decisions (Eq. SP0) of
+                // the current stage pair along the state's survivor.  Odd
+                // candidates carry + 2^k at the pair's stage k, so the max
+                // itself records "the odd predecessor wins or ties" in bit k
+                // (|4 dm| >= 4 exceeds any j + 2^k difference, and on a tie
+                // the odd candidate is larger by 2^k + j_odd - j_even > 0),
+                // and the winner's own bits below k (its decision at stage
+                // k - 1) travel with it.  After the second stage the fields
+                // are stored and cleared: no per-state decision arithmetic.
+                constexpr uint32_t OFF = (S & 1) ? 0x00020002u : 0x00010001u;
+                uint32_t A4[1 << BETA], A4o[1 << BETA];
+#pragma unroll
+                for (int x = 0; x < (1 << BETA); ++x) {
+                    A4[x] = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
+                    A4o[x] = add_u16x2(A4[x], OFF);
+                }
+                auto butterfly_e = [&](int ra) {
+                    const int rb = ra | (1 << PH);
+                    const uint32_t a = C::alpha(C::rotr((uint32_t)ra, PH) >> 1);
+                    const uint32_t Pa = P[ra], Pb = P[rb];
+                    const uint32_t cb0 = add_u16x2(Pb, A4o[a ^ LV]);        // odd -> j0
+                    const uint32_t cb1 = add_u16x2(Pb, A4o[a ^ MV ^ LV]);   // odd -> j1
+                    P[ra] = addmax_u16x2(Pa, A4[a], cb0);                   // even -> j0
+                    P[rb] = addmax_u16x2(Pa, A4[a ^ MV], cb1);              // even -> j1
+                };
+                auto cross_e = [&](int r) {   // partner register in lane ^ (1 << (PH - LR))
+                    constexpr int lb = PH >= LR ? PH - LR : 0;
+                    const uint32_t xb = ((uint32_t)lane >> lb) & 1u;   // 1: this lane holds R_b (odd)
+                    const uint32_t a = C::alpha(C::rotr((uint32_t)r, PH) >> 1);
+                    const uint32_t own = P[r];
+                    const uint32_t oth = __shfl_xor_sync(gmask, own, 1 << lb);
+                    const uint32_t d_own = xb ? A4o[a ^ MV ^ LV] : A4[a];
+                    const uint32_t d_oth = xb ? A4[a ^ MV] : A4o[a ^ LV];
+                    P[r] = addmax_u16x2(own, d_own, add_u16x2(oth, d_oth));
+                };
+                if constexpr (PH < LR) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        if (!(r & (1 << PH))) butterfly_e(r);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) cross_e(r);
+                }
+                if constexpr (S & 1) {
+                    // record word m: register 8m + i at bits 2i (frame 0) and
+                    // 16 + 2i (frame 1); fields cleared, half by a select
+                    // (ALU) and half by a multiply-add (FMA pipe)
+                    uint32_t rec[NWE];
+#pragma unroll
+                    for (int m = 0; m < NWE; ++m) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int i = 7; i >= 0; --i) {
+                            const int r = 8 * m + i;
+                            const uint32_t d = P[r] & 0x00030003u;
+                            P[r] = (i & 1) ? imad(d, m1, P[r]) : (P[r] & ~0x00030003u);
+                            acc = (i == 7) ? d : imad(acc, four, d);
+                        }
+                        rec[m] = acc;
+                    }
+                    if (tau >= tau_store) store_rec(tau, rec);
+                }
+                return;
+            }
+
             // decision offsets: E0[a] = d(odd->j0) - d(even->j0) + 0x8000 and
             // E1[a] = d(odd->j1) - d(even->j1) + 0x8000 per half, for main output a
             uint32_t E0[1 << BETA], E1[1 << BETA];
@@ -743,8 +870,16 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             uint32_t ref = P[0];
             if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
             const uint32_t t = sub_s16x2(SEED0, ref);
+            if constexpr (EMB) {
+                // unsigned form (metrics use all 16 bits): clamp below at
+                // ref - 4S (or 0), then shift; the same result as the signed form
+                const uint32_t lo = sub_s16x2(max_u16x2(ref, S2), S2);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
+                for (int r = 0; r < NR; ++r) P[r] = add_u16x2(max_u16x2(P[r], lo), t);
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
+            }
         }
         hook();
     }
@@ -794,7 +929,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
-                    dst[r] = (int32_t)v - (int32_t)mn;
+                    dst[r] = ((int32_t)v - (int32_t)mn) / Cfg::SC;
                 }
             }
         }
@@ -811,7 +946,7 @@ template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
 __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     constexpr int NS = 1 << (K - 1);
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW, Cfg::EMB>;
     __shared__ TbState tbs[NT];
     __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
