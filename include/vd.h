@@ -307,8 +307,9 @@ void vd_server_destroy(vd_server *server);
  * generator for latency measurement; the paper has no counterpart).
  *
  * Submits packet i (tag i) when arrival_ns[i] nanoseconds (nondecreasing)
- * have passed since the call started, polling completions meanwhile, until
- * all n packets have completed.  Packet i: code_id[i], llr_type[i],
+ * have passed since the call started — for host packets with n >= 4096
+ * from 4 submitting threads, packet i from thread i mod 4 — while the
+ * calling thread collects completions, until all n packets have completed.  Packet i: code_id[i], llr_type[i],
  * n_values[i] values at host_llr + llr_offset[i] bytes, n_info[i], flags[i].
  * Outputs: latency_ns[i] = completion time - submit time (host steady clock,
  * -1 if unfinished); if words is not NULL, packet i's decoded words at
@@ -325,7 +326,8 @@ vd_status vd_server_replay(vd_server *server, int64_t n, const int32_t *code_id,
                            const int64_t *word_offset, int64_t *span_ns);
 
 /* vd_server_replay with the packets' values in device memory (d_llr +
- * llr_offset[i] bytes), submitted with vd_server_submit_device. */
+ * llr_offset[i] bytes), submitted with vd_server_submit_device from one
+ * submitting thread. */
 vd_status vd_server_replay_device(vd_server *server, int64_t n, const int32_t *code_id, const int32_t *llr_type,
                                   const void *d_llr, const int64_t *llr_offset, const int64_t *n_values,
                                   const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,

@@ -23,6 +23,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -643,6 +644,8 @@ extern "C" void vd_server_destroy(vd_server *s) {
 
 namespace {
 
+constexpr int kReplayProducers = 4;   // submitting threads of a long replay
+
 vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_id, const int32_t *llr_type,
                       const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
                       const int64_t *n_info, const uint32_t *flags, const int64_t *arrival_ns,
@@ -669,39 +672,76 @@ vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_
     const uint8_t *base = (const uint8_t *)host_llr;
     const int64_t t0 = now_ns();
     const int64_t deadline = timeout_ms > 0 ? t0 + timeout_ms * 1000000 : INT64_MAX;
-    int64_t next = 0, done = 0, first_submit = INT64_MAX, last_done = t0;
+
+    // Producers: packet i is submitted by thread i mod n_prod at its arrival
+    // time.  Host packets are copied at submit, which several producers (as
+    // from several receivers) share; device packets cost only the queue
+    // insertion, which one producer does faster than several contending for
+    // the queue lock.  This thread collects completions.
+    const int n_prod = (!device && n >= 4096) ? kReplayProducers : 1;
+    std::atomic<bool> abort{false};
+    std::atomic<int> err{VD_OK};
+    std::string err_msg;
+    std::mutex err_mu;
+    auto producer = [&](int tid) {
+        for (int64_t i = tid; i < n && !abort.load(std::memory_order_relaxed); i += n_prod) {
+            for (;;) {
+                const int64_t now = now_ns();
+                const int64_t wait = arrival_ns[i] - (now - t0);
+                if (wait <= 0) break;
+                if (now > deadline || abort.load(std::memory_order_relaxed)) return;
+                if (wait > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+                else std::this_thread::yield();
+            }
+            const vd_status st = submit_common(s, code_id[i], llr_type[i], base + llr_offset[i], device,
+                                               n_values[i], n_info[i], flags[i], (uint64_t)i);
+            if (st != VD_OK) {
+                std::lock_guard<std::mutex> lk(err_mu);
+                if (err.load() == VD_OK) err_msg = vd_last_error();
+                err.store(st);
+                abort.store(true);
+                return;
+            }
+        }
+    };
+    std::vector<std::thread> prods;
+    for (int t = 0; t < n_prod; ++t) prods.emplace_back(producer, t);
+    auto finish = [&](vd_status st) {
+        abort.store(true);
+        for (auto &th : prods) th.join();
+        return st;
+    };
+
+    int64_t done = 0, first_submit = INT64_MAX, last_done = t0;
     while (done < n) {
-        const int64_t now = now_ns();
-        if (now > deadline) {
+        if (err.load() != VD_OK) {
+            finish(VD_OK);
+            return fail((vd_status)err.load(), "replay: submit failed: %s", err_msg.c_str());
+        }
+        if (now_ns() > deadline) {
+            finish(VD_OK);
             if (span_ns) *span_ns = last_done - (first_submit == INT64_MAX ? t0 : first_submit);
             return fail(VD_ETIMEOUT, "replay: %lld of %lld packets done after %lld ms", (long long)done,
                         (long long)n, (long long)timeout_ms);
-        }
-        while (next < n && arrival_ns[next] <= now - t0) {
-            const vd_status st = submit_common(s, code_id[next], llr_type[next], base + llr_offset[next], device,
-                                               n_values[next], n_info[next], flags[next], (uint64_t)next);
-            if (st != VD_OK) return st;
-            ++next;
         }
         const int64_t k = vd_server_poll(s, comp.data(), cap_comp, wbuf.data(), cap_words);
         for (int64_t j = 0; j < k; ++j) {
             const vd_completion &c = comp[(size_t)j];
             const int64_t i = (int64_t)c.tag;
             if (i < 0 || i >= n) continue;
-            if (c.status != VD_OK) return fail(VD_ECUDA, "replay: the device reported an error");
+            if (c.status != VD_OK) {
+                finish(VD_OK);
+                return fail(VD_ECUDA, "replay: the device reported an error");
+            }
             latency_ns[i] = c.done_ns - c.submit_ns;
             first_submit = std::min(first_submit, c.submit_ns);
             last_done = std::max(last_done, c.done_ns);
             if (words) memcpy(words + word_offset[i], wbuf.data() + c.word_offset, (size_t)c.n_words * 4);
             ++done;
         }
-        if (k == 0) {
-            // nothing finished: wait for the next arrival (spinning when it is close)
-            const int64_t wait = next < n ? arrival_ns[next] - (now_ns() - t0) : 20000;
-            if (wait > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-            else if (wait > 0) std::this_thread::yield();
-        }
+        if (k == 0) std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
+    finish(VD_OK);
     if (span_ns) *span_ns = n ? last_done - first_submit : 0;
     return VD_OK;
 }
