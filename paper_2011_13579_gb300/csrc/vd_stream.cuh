@@ -640,10 +640,24 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 // are stored and cleared: no per-state decision arithmetic.
                 constexpr uint32_t OFF = (S & 1) ? 0x00020002u : 0x00010001u;
                 uint32_t A4[1 << BETA], A4o[1 << BETA];
+                if constexpr (COROLLARY) {
+                    // complement patterns have the negated metric: scale half
+                    // of the table, negate per half (~x + 1) for the rest
+                    constexpr int FULL = (1 << BETA) - 1;
 #pragma unroll
-                for (int x = 0; x < (1 << BETA); ++x) {
-                    A4[x] = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
-                    A4o[x] = add_u16x2(A4[x], OFF);
+                    for (int x = 0; x < (1 << (BETA - 1)); ++x) {
+                        A4[x] = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
+                        const uint32_t n = ~A4[x];
+                        A4[x ^ FULL] = add_u16x2(n, 0x00010001u);
+                        A4o[x] = add_u16x2(A4[x], OFF);
+                        A4o[x ^ FULL] = add_u16x2(n, 0x00010001u + OFF);
+                    }
+                } else {
+#pragma unroll
+                    for (int x = 0; x < (1 << BETA); ++x) {
+                        A4[x] = (A[x] << 2) & 0xFFFCFFFCu;
+                        A4o[x] = add_u16x2(A4[x], OFF);
+                    }
                 }
                 auto butterfly_e = [&](int ra) {
                     const int rb = ra | (1 << PH);
