@@ -98,18 +98,23 @@ __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks,
         FrameTask ft[2];
         pair_of((int64_t)t * PPW + group, ft);
         TbState &pend = tbs[cur][threadIdx.x];
+        typename Tb::Live live;
         if constexpr (NREC == 2) {
             TbState &next = tbs[cur ^ 1][threadIdx.x];
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, next,
-                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+                [&](auto Sc) {
+                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             cur ^= 1;
         } else {
             TbState tb;
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, tb,
-                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+                [&](auto Sc) {
+                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             pend = tb;
         }
@@ -163,18 +168,23 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
             ft[1] = ft[0];
         }
         TbState &pend = tbs[cur][threadIdx.x];
+        typename Tb::Live live;
         if constexpr (NREC == 2) {
             TbState &next = tbs[cur ^ 1][threadIdx.x];
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, next,
-                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+                [&](auto Sc) {
+                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             cur ^= 1;
         } else {
             TbState tb;
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, tb,
-                [&] { Tb::step(pend, my_stg, wlane, lane, gmask, grp_base); });
+                [&](auto Sc) {
+                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             pend = tb;
         }

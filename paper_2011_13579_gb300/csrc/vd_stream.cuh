@@ -300,18 +300,33 @@ struct Traceback {
         issue(s, s.t0 - G, stg + SLOT_WORDS, wlane);
     }
 
-    // Walks one group (if any remains) and refills its slot with the group two ahead.
-    __device__ static void step(TbState &s, uint32_t *stg, int wlane, int lane, unsigned gmask,
-                                int grp_base) {
-        if (!active(s)) return;
-        cp_async_wait<1>();
-        const uint32_t *slot = stg + s.slot * SLOT_WORDS;
-        const int t0 = s.t0;
-        const int tl = t0 - (G - 1);   // lowest stage of the group
-        uint32_t Rh[2] = {s.R[0], s.R[1]};
-        const uint32_t Rs[2] = {Rh[0], Rh[1]};
+    // A group walk in pieces: open() before the group's first record,
+    // walk<j>() per record, close() after the last.  The persistent kernels
+    // call them from the stages of a forward chunk (sub<S>), so the walk's
+    // dependent chain (record word -> rotate -> select -> next word) spreads
+    // over the chunk instead of stalling the warp at its end.
+    static constexpr int STEPS = EMB ? G / 2 : (RADIX4 ? G / 2 : G);   // walk<> calls per group
+    struct Live {
+        uint32_t R[2];           // traceback registers of both frames
+        const uint32_t *slot;    // staging slot of the group
+        bool act;
+    };
+
+    __device__ static void open(const TbState &s, const uint32_t *stg, Live &v) {
+        v.act = active(s);
+        if (v.act) {
+            cp_async_wait<1>();
+            v.slot = stg + s.slot * SLOT_WORDS;
+            v.R[0] = s.R[0];
+            v.R[1] = s.R[1];
+        }
+    }
+
+    template <int j>
+    __device__ static void walk(Live &v, int wlane, unsigned gmask, int grp_base) {
+        if (!v.act) return;
         auto words = [&](int g, uint32_t (&wd)[RW]) {
-            const uint32_t *p = slot + (g * 32 + wlane) * RW;
+            const uint32_t *p = v.slot + (g * 32 + wlane) * RW;
             if constexpr (RW == 1) {
                 wd[0] = p[0];
             } else if constexpr (RW == 2) {
@@ -327,7 +342,7 @@ struct Traceback {
         };
         // The survivor word of register R in frame h, rotated right so that
         // R's decision bit lands at bit position ph.
-        auto rotated = [&](const uint32_t (&wd)[NW], int h, uint32_t R, int ph) -> uint32_t {
+        auto rotated = [&](const uint32_t (&wd)[RW], int h, uint32_t R, int ph) -> uint32_t {
             uint32_t word, bit;
             if constexpr (NR >= 32) {
                 word = pick<WPF>(&wd[h * WPF], (R >> 5) & (uint32_t)(WPF - 1));
@@ -348,65 +363,64 @@ struct Traceback {
             // t-1 of the register it came from (bit 0).  The phases of t and
             // t-1 are adjacent (t's is odd), so one rotation puts both bits in
             // place and one select replaces both bits of R.
-            static_for<REC>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                constexpr int ph1 = ((NB - 1 - 2 * j) % NB + NB) % NB;
-                constexpr int ph0 = ph1 - 1;
-                static_assert(ph1 >= 1, "the second stage of a pair has an odd phase");
-                constexpr uint32_t m = 3u << ph0;
-                uint32_t wd[RW];
-                words(j, wd);
+            constexpr int ph1 = ((NB - 1 - 2 * j) % NB + NB) % NB;
+            constexpr int ph0 = ph1 - 1;
+            static_assert(ph1 >= 1, "the second stage of a pair has an odd phase");
+            constexpr uint32_t m = 3u << ph0;
+            const uint32_t *rec = v.slot + (j * 32 + wlane) * RW;   // this lane's record
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t R = Rh[h];
-                    const uint32_t word = RW == 1 ? wd[0] : pick<RW>(wd, (R >> 3) & (uint32_t)(RW - 1));
-                    const uint32_t sh = 2u * (R & 7u) + 16u * (uint32_t)h;
-                    const uint32_t t = owner(__funnelshift_r(word, word, sh - (uint32_t)ph0), R);
-                    Rh[h] = (R & ~m) | (t & m);
-                }
-            });
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t R = v.R[h];
+                const uint32_t word = rec[(R >> 3) & (uint32_t)(RW - 1)];   // the word holding R
+                const uint32_t sh = 2u * (R & 7u) + 16u * (uint32_t)h;
+                const uint32_t t = owner(__funnelshift_r(word, word, sh - (uint32_t)ph0), R);
+                v.R[h] = (R & ~m) | (t & m);
+            }
         } else if constexpr (!RADIX4) {
-            static_for<G>([&](auto gc) {
-                constexpr int g = decltype(gc)::value;
-                constexpr int ph = ((NB - 1 - g) % NB + NB) % NB;   // group starts at -1 mod (K-1)
-                uint32_t wd[NW];
-                words(g, wd);
+            constexpr int ph = ((NB - 1 - j) % NB + NB) % NB;   // group starts at -1 mod (K-1)
+            uint32_t wd[RW];
+            words(j, wd);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t t = owner(rotated(wd, h, Rh[h], ph), Rh[h]);
-                    Rh[h] = (Rh[h] & ~(1u << ph)) | (t & (1u << ph));
-                }
-            });
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t t = owner(rotated(wd, h, v.R[h], ph), v.R[h]);
+                v.R[h] = (v.R[h] & ~(1u << ph)) | (t & (1u << ph));
+            }
         } else {
             // pairs (t, t-1): t is the second stage of a pair; both decisions
             // of register R sit at the same bit position in the two words
-            static_for<G / 2>([&](auto gc) {
-                constexpr int g = 2 * decltype(gc)::value;
-                constexpr int ph2 = ((NB - 1 - g) % NB + NB) % NB;
-                constexpr int ph1 = ((NB - 2 - g) % NB + NB) % NB;
-                constexpr uint32_t m2 = 1u << ph2, m1 = 1u << ph1;
-                uint32_t w2[NW], w1[NW];
-                words(g, w2);
-                words(g + 1, w1);
+            constexpr int g = 2 * j;
+            constexpr int ph2 = ((NB - 1 - g) % NB + NB) % NB;
+            constexpr int ph1 = ((NB - 2 - g) % NB + NB) % NB;
+            constexpr uint32_t m2 = 1u << ph2, m1 = 1u << ph1;
+            uint32_t w2[RW], w1[RW];
+            words(g, w2);
+            words(g + 1, w1);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t t2 = rotated(w2, h, Rh[h], ph2);
-                    const uint32_t t1 = rotated(w1, h, Rh[h], ph1);
-                    const uint32_t t = owner((t2 & m2) | (t1 & ~m2), Rh[h]);
-                    Rh[h] = (Rh[h] & ~(m2 | m1)) | (t & (m2 | m1));
-                }
-            });
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t t2 = rotated(w2, h, v.R[h], ph2);
+                const uint32_t t1 = rotated(w1, h, v.R[h], ph1);
+                const uint32_t t = owner((t2 & m2) | (t1 & ~m2), v.R[h]);
+                v.R[h] = (v.R[h] & ~(m2 | m1)) | (t & (m2 | m1));
+            }
         }
+    }
+
+    // Emits the group's decoded bits, refills its slot with the group two
+    // ahead and advances.
+    __device__ static void close(TbState &s, uint32_t *stg, const Live &v, int wlane, int lane) {
+        if (!v.act) return;
+        const int t0 = s.t0;
+        const int tl = t0 - (G - 1);   // lowest stage of the group
         // Each bit position of R is replaced once per group, so the group's
         // decoded bits (the input bit of each stage's state) are the bits of
-        // R at the start of the group: stage tl + i is bit i.
+        // R at the start of the group (still in s.R): stage tl + i is bit i.
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int lo = tl > s.tauo[h] ? tl : s.tauo[h];
             const int hi = (t0 + 1) < s.taue[h] ? (t0 + 1) : s.taue[h];
             if (hi > lo) {
                 const int m = hi - lo;
-                const uint64_t bits = (uint64_t)((Rs[h] >> (lo - tl)) & ((1u << m) - 1u));
+                const uint64_t bits = (uint64_t)((s.R[h] >> (lo - tl)) & ((1u << m) - 1u));
                 uint64_t acc = (s.oacc[h] << m) | bits;
                 int nb = s.onb[h] + m;
                 const int a = lo + s.toff[h];              // stream stage of bit 0
@@ -420,12 +434,33 @@ struct Traceback {
                 s.onb[h] = nb;
             }
         }
-        s.R[0] = Rh[0];
-        s.R[1] = Rh[1];
+        s.R[0] = v.R[0];
+        s.R[1] = v.R[1];
         // refill the consumed slot with the group two ahead, then advance
         issue(s, t0 - 2 * G, stg + s.slot * SLOT_WORDS, wlane);
         s.t0 = t0 - G;
         s.slot ^= 1;
+    }
+
+    // The pieces that belong after stage S of a forward chunk (chunks are a
+    // whole number of groups).
+    template <int S>
+    __device__ static void sub(TbState &s, uint32_t *stg, Live &v, int wlane, int lane, unsigned gmask,
+                               int grp_base) {
+        constexpr int Sg = S % G;
+        constexpr int SPS = G / STEPS;   // stages per walk step
+        if constexpr (Sg == 0) open(s, stg, v);
+        if constexpr (Sg % SPS == SPS - 1) walk<Sg / SPS>(v, wlane, gmask, grp_base);
+        if constexpr (Sg == G - 1) close(s, stg, v, wlane, lane);
+    }
+
+    // Walks one group (if any remains) and refills its slot with the group two ahead.
+    __device__ static void step(TbState &s, uint32_t *stg, int wlane, int lane, unsigned gmask,
+                                int grp_base) {
+        Live v;
+        open(s, stg, v);
+        static_for<STEPS>([&](auto jc) { walk<decltype(jc)::value>(v, wlane, gmask, grp_base); });
+        close(s, stg, v, wlane, lane);
     }
 
     // Walks every remaining group and waits for all copies.
@@ -439,8 +474,9 @@ struct Traceback {
 // Forward procedure (Algorithm 1) and survivor storage for one pair of frames.
 // Called by one group of L lanes; surv is the frame pair's survivor buffer in
 // this warp's scratch (wpad_cap stages x 32 lanes x NW words); wlane is the
-// lane in the warp.  hook() runs after every chunk of U stages (the
-// persistent kernel walks a previous pair's traceback there).  On return tb
+// lane in the warp.  hook(integral_constant<int, S>) runs after stage S of
+// every chunk of U stages (the persistent kernels walk a previous pair's
+// traceback there, a piece per stage).  On return tb
 // holds the traceback start of this pair; returns false (tb inactive) if the
 // pair does not fit the scratch, which host plans never produce.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, typename Hook>
@@ -705,6 +741,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     }
                     if (tau >= tau_store) store_rec(tau, rec);
                 }
+                hook(Sc);
                 return;
             }
 
@@ -877,6 +914,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     store_words(tau - 1, lo_w);
                 }
             }
+            hook(Sc);
         });
 
         // ---- normalisation: subtract state 0's metric, add F+S, clamp at F
@@ -895,7 +933,6 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
             }
         }
-        hook();
     }
 
     // ------------------------------------------------- traceback start state
@@ -980,7 +1017,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::NW;
     TbState &st = tbs[threadIdx.x];
     forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
-                                           st, [] {});
+                                           st, [](auto) {});
     uint32_t *my_stg = stg[threadIdx.x >> 5];
     if (Tb::active(st)) {
         Tb::begin(st, my_stg, wlane);
