@@ -226,10 +226,13 @@ __host__ __device__ constexpr uint32_t bitk_mask(int k) {
 // Survivor words: bit (r & 31) of word (r >> 5) holds register r of the lane
 // (r & 15 at bit 16h when a lane has 16 registers or fewer), frame 0 first.
 
+// All fields are 32-bit words (pointers and the 64-bit bit accumulator are
+// split in two): 23 words, an odd stride, so the per-thread records in shared
+// memory are read and written without bank conflicts.
 struct TbState {
-    uint32_t *out[2];        // packed output of each frame's stream
-    const uint32_t *surv;    // this lane's survivor words (stage stride 32 * NW words)
-    uint64_t oacc[2];        // decoded bits not yet stored: bit i = stage (lowest emitted + i)
+    uint32_t out_w[2][2];    // packed output of each frame's stream (pointer words)
+    uint32_t surv_w[2];      // this lane's survivor records (pointer words)
+    uint32_t oacc_w[2][2];   // decoded bits not yet stored: bit i = stage (lowest emitted + i)
     uint32_t R[2];           // current register of each frame (traceback state)
     int32_t onb[2];          // number of bits in oacc
     int32_t t0;              // first stage of the next group; finished when t0 < tau_store
@@ -237,8 +240,33 @@ struct TbState {
     int32_t tauo[2], taue[2];
     int32_t toff[2];         // stage in the frame's stream = tau + toff
     int32_t slot;            // staging slot holding group t0
-    int32_t pad;
+
+    __device__ __forceinline__ static uint64_t join(uint32_t lo, uint32_t hi) {
+        return ((uint64_t)hi << 32) | lo;
+    }
+    __device__ __forceinline__ uint32_t *out(int h) const {
+        return reinterpret_cast<uint32_t *>(join(out_w[h][0], out_w[h][1]));
+    }
+    __device__ __forceinline__ void set_out(int h, uint32_t *p) {
+        const uint64_t x = reinterpret_cast<uint64_t>(p);
+        out_w[h][0] = (uint32_t)x;
+        out_w[h][1] = (uint32_t)(x >> 32);
+    }
+    __device__ __forceinline__ const uint32_t *surv() const {
+        return reinterpret_cast<const uint32_t *>(join(surv_w[0], surv_w[1]));
+    }
+    __device__ __forceinline__ void set_surv(const uint32_t *p) {
+        const uint64_t x = reinterpret_cast<uint64_t>(p);
+        surv_w[0] = (uint32_t)x;
+        surv_w[1] = (uint32_t)(x >> 32);
+    }
+    __device__ __forceinline__ uint64_t oacc(int h) const { return join(oacc_w[h][0], oacc_w[h][1]); }
+    __device__ __forceinline__ void set_oacc(int h, uint64_t v) {
+        oacc_w[h][0] = (uint32_t)v;
+        oacc_w[h][1] = (uint32_t)(v >> 32);
+    }
 };
+static_assert(sizeof(TbState) == 23 * 4 && alignof(TbState) == 4, "odd-word traceback record");
 
 __device__ __forceinline__ void cp_async_bytes16(void *smem, const void *gmem) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -277,7 +305,7 @@ struct Traceback {
             const int t = t0 - (EMB ? 2 * g : g);   // EMB: the second stage of a pair
             if (t >= s.tau_store) {
                 uint32_t *dst = slot + (g * 32 + wlane) * RW;
-                const uint32_t *src = s.surv + (size_t)(EMB ? (t >> 1) : t) * 32 * RW;
+                const uint32_t *src = s.surv() + (size_t)(EMB ? (t >> 1) : t) * 32 * RW;
                 if constexpr (RW == 1) {
                     cp_async_bytes4(dst, src);
                 } else if constexpr (RW == 2) {
@@ -421,16 +449,16 @@ struct Traceback {
             if (hi > lo) {
                 const int m = hi - lo;
                 const uint64_t bits = (uint64_t)((s.R[h] >> (lo - tl)) & ((1u << m) - 1u));
-                uint64_t acc = (s.oacc[h] << m) | bits;
+                uint64_t acc = (s.oacc(h) << m) | bits;
                 int nb = s.onb[h] + m;
                 const int a = lo + s.toff[h];              // stream stage of bit 0
                 const int wb = (a + nb - 1) & ~31;         // first stage of the top word
                 if (a <= wb) {
-                    if (lane == (L > 1 ? h : 0)) s.out[h][wb >> 5] = (uint32_t)(acc >> (wb - a));
+                    if (lane == (L > 1 ? h : 0)) s.out(h)[wb >> 5] = (uint32_t)(acc >> (wb - a));
                     nb = wb - a;
                     acc &= (1ull << nb) - 1ull;
                 }
-                s.oacc[h] = acc;
+                s.set_oacc(h, acc);
                 s.onb[h] = nb;
             }
         }
@@ -526,10 +554,11 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
 
     // the traceback's fixed parameters are written now (tb may live in
     // shared memory), so they hold no registers during the forward pass
-    tb.out[0] = ft[0].out;
-    tb.out[1] = ft[1].out;
-    tb.surv = surv + (size_t)wlane * (EMB ? NWE : NW);
-    tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.set_out(0, ft[0].out);
+    tb.set_out(1, ft[1].out);
+    tb.set_surv(surv + (size_t)wlane * (EMB ? NWE : NW));
+    tb.set_oacc(0, 0u);
+    tb.set_oacc(1, 0u);
     tb.onb[0] = tb.onb[1] = 0;
     tb.tau_store = tau_store;
 #pragma unroll

@@ -250,12 +250,13 @@ __device__ __forceinline__ bool forward_pair_f32(const FrameTask (&ft)[2], uint3
         }
         R[h] = term[h] ? 0u : bR;
     }
-    tb.out[0] = ft[0].out;
-    tb.out[1] = ft[1].out;
-    tb.surv = surv + (size_t)wlane * NW;
+    tb.set_out(0, ft[0].out);
+    tb.set_out(1, ft[1].out);
+    tb.set_surv(surv + (size_t)wlane * NW);
     tb.R[0] = R[0];
     tb.R[1] = R[1];
-    tb.oacc[0] = tb.oacc[1] = 0u;
+    tb.set_oacc(0, 0u);
+    tb.set_oacc(1, 0u);
     tb.onb[0] = tb.onb[1] = 0;
     tb.t0 = Wpad - 1;
     tb.tau_store = tau_store;
