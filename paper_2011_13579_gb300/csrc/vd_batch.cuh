@@ -89,6 +89,8 @@ __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks,
     int cur = 0;   // record of the pair being traced back
     tbs[0][threadIdx.x].t0 = -1;
     tbs[0][threadIdx.x].tau_store = 0;
+    tbs[0][threadIdx.x].slot = 0;
+    tbs[0][threadIdx.x].R[0] = tbs[0][threadIdx.x].R[1] = 0;
     int buf = 0;
     while (true) {
         int t = 0;
@@ -151,6 +153,8 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     int cur = 0;   // record of the pair being traced back
     tbs[0][threadIdx.x].t0 = -1;
     tbs[0][threadIdx.x].tau_store = 0;
+    tbs[0][threadIdx.x].slot = 0;
+    tbs[0][threadIdx.x].R[0] = tbs[0][threadIdx.x].R[1] = 0;
     int buf = 0;
     while (true) {
         int t = 0;

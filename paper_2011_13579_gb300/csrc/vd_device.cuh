@@ -27,6 +27,10 @@
 //     and carries the winner's lower bit along; the fields are stored and
 //     cleared after the pair.  With the scale the bound becomes
 //     4 (F + 2S + (N+1) B) + 3 <= 65535 (unsigned halves), N = 18 for K=7.
+//     Its normalisation is folded into the branch metrics of the next stage
+//     (every candidate gets + 4(F+S) - ref) and needs no clamp: only states
+//     not yet reachable from a head-start state 0 fall below the reference,
+//     for fewer than K-1 stages, and F >= (3(K-1)+1) B keeps them >= 0.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

@@ -134,6 +134,11 @@ struct StreamCfg {
                       : F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767,
                   "metric range");
     static_assert(!EMB || NWE * 16 <= 32 * NW, "a stage pair's records fit the per-stage scratch");
+    // The embedded form normalises without a clamp.  Below the reference
+    // only states not yet reachable from a head-start state 0 can fall (for
+    // fewer than K-1 stages), by at most 2(K-1)B before and (K-1)B + B after
+    // a normalisation, so a floor F >= (3(K-1) + 1) B keeps them >= 0.
+    static_assert(!EMB || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
 };
 
 template <typename Fn, int... S>
@@ -329,10 +334,7 @@ struct Traceback {
     }
 
     // A group walk in pieces: open() before the group's first record,
-    // walk<j>() per record, close() after the last.  The persistent kernels
-    // call them from the stages of a forward chunk (sub<S>), so the walk's
-    // dependent chain (record word -> rotate -> select -> next word) spreads
-    // over the chunk instead of stalling the warp at its end.
+    // walk<j>() per record, close() after the last.
     static constexpr int STEPS = EMB ? G / 2 : (RADIX4 ? G / 2 : G);   // walk<> calls per group
     struct Live {
         uint32_t R[2];           // traceback registers of both frames
@@ -340,19 +342,20 @@ struct Traceback {
         bool act;
     };
 
+    // Branch-free: an inactive walk (act false) reads in-bounds staging words
+    // and changes nothing that close() keeps, so the embedded-decision walk
+    // runs unconditionally (measured 3% faster than a branch around it).
     __device__ static void open(const TbState &s, const uint32_t *stg, Live &v) {
         v.act = active(s);
-        if (v.act) {
-            cp_async_wait<1>();
-            v.slot = stg + s.slot * SLOT_WORDS;
-            v.R[0] = s.R[0];
-            v.R[1] = s.R[1];
-        }
+        cp_async_wait<1>();
+        v.slot = stg + (s.slot & 1) * SLOT_WORDS;
+        v.R[0] = s.R[0] & (uint32_t)((1 << NB) - 1);
+        v.R[1] = s.R[1] & (uint32_t)((1 << NB) - 1);
     }
 
     template <int j>
     __device__ static void walk(Live &v, int wlane, unsigned gmask, int grp_base) {
-        if (!v.act) return;
+        if (!EMB && !v.act) return;
         auto words = [&](int g, uint32_t (&wd)[RW]) {
             const uint32_t *p = v.slot + (g * 32 + wlane) * RW;
             if constexpr (RW == 1) {
@@ -470,16 +473,14 @@ struct Traceback {
         s.slot ^= 1;
     }
 
-    // The pieces that belong after stage S of a forward chunk (chunks are a
-    // whole number of groups).
+    // The traceback work that belongs after stage S of a forward chunk
+    // (chunks are a whole number of groups): one group after the group's
+    // last stage.  (Spreading the records over the stages was measured 2%
+    // slower: the forward stages schedule better as whole blocks.)
     template <int S>
-    __device__ static void sub(TbState &s, uint32_t *stg, Live &v, int wlane, int lane, unsigned gmask,
+    __device__ static void sub(TbState &s, uint32_t *stg, Live &, int wlane, int lane, unsigned gmask,
                                int grp_base) {
-        constexpr int Sg = S % G;
-        constexpr int SPS = G / STEPS;   // stages per walk step
-        if constexpr (Sg == 0) open(s, stg, v);
-        if constexpr (Sg % SPS == SPS - 1) walk<Sg / SPS>(v, wlane, gmask, grp_base);
-        if constexpr (Sg == G - 1) close(s, stg, v, wlane, lane);
+        if constexpr (S % G == G - 1) step(s, stg, wlane, lane, gmask, grp_base);
     }
 
     // Walks one group (if any remains) and refills its slot with the group two ahead.
@@ -504,7 +505,7 @@ struct Traceback {
 // this warp's scratch (wpad_cap stages x 32 lanes x NW words); wlane is the
 // lane in the warp.  hook(integral_constant<int, S>) runs after stage S of
 // every chunk of U stages (the persistent kernels walk a previous pair's
-// traceback there, a piece per stage).  On return tb
+// traceback there, a group per K-1 stages).  On return tb
 // holds the traceback start of this pair; returns false (tb inactive) if the
 // pair does not fit the scratch, which host plans never produce.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, typename Hook>
@@ -537,6 +538,8 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const int Wpad = (int)(((Wmax + U - 1) / U) * U);
     tb.t0 = -1;
     tb.tau_store = 0;
+    tb.slot = 0;
+    tb.R[0] = tb.R[1] = 0;
     if (Wpad > wpad_cap) {   // never happens for plans built by the host; refuse, do not overrun
         if (lane == 0) atomicOr(status, 1);
         return false;
@@ -644,6 +647,19 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             finish_chunk<UW>(fbase1, cb1, hi1, cur1, cw1);
         }
         uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
+        // embedded form: the normalisation of every NORM_CHUNKS-th chunk
+        // boundary is folded into the branch metrics of the chunk's first
+        // stage (adding tn to every candidate shifts every new metric by tn,
+        // as normalising before the stage would).  tn = 4(F+S) - (metric of
+        // state 0), or 0 between normalisations.
+        uint32_t tn = 0, tn1 = 0, tn2 = 0;
+        if constexpr (EMB) {
+            uint32_t ref = P[0];
+            if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
+            tn = (c > 0 && c % Cfg::NORM_CHUNKS == 0) ? sub_s16x2(SEED0, ref) : 0u;
+            tn1 = add_u16x2(tn, 0x00010001u);   // -x + tn = ~x + tn1
+            tn2 = add_u16x2(tn, 0x00020002u);   // -x + 1 + tn (odd candidates of stage 0)
+        }
 
         static_for<U>([&](auto Sc) {
             constexpr int S = decltype(Sc)::value;
@@ -711,16 +727,24 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     constexpr int FULL = (1 << BETA) - 1;
 #pragma unroll
                     for (int x = 0; x < (1 << (BETA - 1)); ++x) {
-                        A4[x] = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
-                        const uint32_t n = ~A4[x];
-                        A4[x ^ FULL] = add_u16x2(n, 0x00010001u);
+                        const uint32_t a4 = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
+                        const uint32_t n = ~a4;
+                        if constexpr (S == 0) {   // with the folded normalisation
+                            A4[x] = add_u16x2(a4, tn);
+                            A4[x ^ FULL] = add_u16x2(n, tn1);
+                            A4o[x ^ FULL] = add_u16x2(n, tn2);
+                        } else {
+                            A4[x] = a4;
+                            A4[x ^ FULL] = add_u16x2(n, 0x00010001u);
+                            A4o[x ^ FULL] = add_u16x2(n, 0x00010001u + OFF);
+                        }
                         A4o[x] = add_u16x2(A4[x], OFF);
-                        A4o[x ^ FULL] = add_u16x2(n, 0x00010001u + OFF);
                     }
                 } else {
 #pragma unroll
                     for (int x = 0; x < (1 << BETA); ++x) {
                         A4[x] = (A[x] << 2) & 0xFFFCFFFCu;
+                        if constexpr (S == 0) A4[x] = add_u16x2(A4[x], tn);
                         A4o[x] = add_u16x2(A4[x], OFF);
                     }
                 }
@@ -947,20 +971,12 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
         });
 
         // ---- normalisation: subtract state 0's metric, add F+S, clamp at F
-        if ((c + 1) % Cfg::NORM_CHUNKS == 0) {
+        if (!EMB && (c + 1) % Cfg::NORM_CHUNKS == 0) {
             uint32_t ref = P[0];
             if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
             const uint32_t t = sub_s16x2(SEED0, ref);
-            if constexpr (EMB) {
-                // unsigned form (metrics use all 16 bits): clamp below at
-                // ref - 4S (or 0), then shift; the same result as the signed form
-                const uint32_t lo = sub_s16x2(max_u16x2(ref, S2), S2);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) P[r] = add_u16x2(max_u16x2(P[r], lo), t);
-            } else {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
-            }
+            for (int r = 0; r < NR; ++r) P[r] = max_s16x2(add_s16x2(P[r], t), F2);
         }
     }
 
