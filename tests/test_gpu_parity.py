@@ -183,6 +183,30 @@ def test_edge_cases_k7(n, f, v, term, unk, kind, radix):
         check(gw, gpm, ow, opm, 7, n, f, v, T, term, unk)
 
 
+@pytest.mark.parametrize("kind", ["saturated", "noisy"])
+def test_head_start_near_normalisation_k7(kind):
+    """The first frame's head-start stage swept over every residue of the
+    metric normalisation period (18 stages for the K=7 integer form): the
+    overlap v moves the start of the first frame inside its padded pair, so
+    some resets fall within K-1 stages before a normalisation, where states
+    not yet reachable from state 0 sit lowest.  Saturated LLRs make the
+    metric spread as large as the bound allows."""
+    oc = oracle.Code(7, synth.K7_GENS)
+    code = gpu_code(7, synth.K7_GENS)
+    n, f = 600, 64
+    for v in range(6, 42):
+        rng = np.random.Generator(np.random.PCG64(3000 + v))
+        for term in (False, True):
+            T = n + (6 if term else 0)
+            if kind == "saturated":
+                q = (127 * (1 - 2 * rng.integers(0, 2, 2 * T))).astype(np.int8)
+            else:
+                q = synth.make_stream(rng, 7, synth.K7_GENS, n, 1.0, term).s8()
+            ow, opm = run_oracle(oc, q.reshape(T, 2).astype(np.int32), n, f, v, term)
+            gw, gpm = run_gpu(code, q, n, f, v, terminated=term, lanes=1)
+            check(gw, gpm, ow, opm, 7, n, f, v, T, term, False)
+
+
 @pytest.mark.parametrize("n,f,v,term", [(1, 32, 8, True), (70, 64, 3, False), (2000, 512, 64, True),
                                         (2049, 1024, 700, False)])
 @pytest.mark.parametrize("kind", ["noisy", "zeros", "erasures"])
