@@ -374,7 +374,7 @@ vd_status vd_sync(void *stream);
  * bytes (32 MiB), which occupies that much memory on every GPU where the
  * library's device code is loaded, until the process exits.  A stream whose
  * scratch would not fit is rejected with VD_EINVAL and a message giving both
- * sizes (for the K=7 code at f=256, v=42 this is about 3 million info bits).
+ * sizes (for the K=7 code at f=256, v=42 this is about 2 million info bits).
  *
  * Arguments as vd_decode, restricted to unpunctured int8 LLRs (VD_LLR_S8);
  * no metric output.  The first call on each device looks up the device

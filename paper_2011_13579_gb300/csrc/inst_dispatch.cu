@@ -64,7 +64,7 @@ bool geom_k7(int lanes, bool radix4, KernelGeom *g) {
 #define X(K, R4, L)                                                        \
     if (K == 7 && radix4 == R4 && lanes == L) {                            \
         g->U = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::U;   \
-        g->NW = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::NW; \
+        g->NW = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::SW; \
         return true;                                                       \
     }
     VD_VARIANT_LIST(X)
@@ -75,7 +75,7 @@ bool geom_k9(int lanes, bool radix4, KernelGeom *g) {
 #define X(K, R4, L)                                                        \
     if (K == 9 && radix4 == R4 && lanes == L) {                            \
         g->U = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::U;   \
-        g->NW = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::NW; \
+        g->NW = StreamCfg<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4>::SW; \
         return true;                                                       \
     }
     VD_VARIANT_LIST(X)

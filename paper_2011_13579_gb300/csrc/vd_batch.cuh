@@ -36,7 +36,7 @@ struct BatchParams {
     const int8_t *llr_int;    // the internal arena (depunctured / unpacked packets)
     uint32_t *out;            // the caller's output arena
     int *counter;             // task counter, zero at launch
-    uint32_t *surv;           // per resident warp: 2 x wpad_cap x 32 x NW words
+    uint32_t *surv;           // per resident warp: 2 x wpad_cap x 32 x SW words
     int32_t wpad_cap;
     int *status;
 };
@@ -57,33 +57,50 @@ __device__ __forceinline__ FrameTask packet_frame(const BatchParams &p, uint32_t
     return frame_task(llr, p.out + d.out_word_off, nullptr, (int64_t)s, n_win, d.n_info, T, d.f, d.v, fl);
 }
 
+// Shared memory of the persistent kernels, in dynamic shared memory: the
+// per-warp traceback staging (16-byte aligned, first), then NREC traceback
+// records per thread.  Two records per thread when they fit the budget: the
+// forward pass writes the next pair's record in place while the hook walks
+// the previous one, so neither occupies registers.  The three-stage record
+// form (ES = 3) stages 8 KB per warp and needs more than the 48 KB a block
+// gets without opting in; the launchers opt in (cudaFuncSetAttribute).
+template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
+struct PersistentSmem {
+    using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW, Cfg::ES>;
+    static constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
+    static constexpr size_t TB_BYTES = (size_t)NT * sizeof(TbState);
+    static constexpr size_t BUDGET = (Cfg::ES == 3 ? 64u : 48u) * 1024u;
+    static constexpr int NREC = (2 * TB_BYTES + STG_BYTES <= BUDGET) ? 2 : 1;
+    static constexpr size_t BYTES = STG_BYTES + (size_t)NREC * TB_BYTES;
+    static_assert(STG_BYTES % 16 == 0, "records follow the staging at a 16-byte boundary");
+};
+
 // The persistent decode loop.  Each resident warp pulls tasks of 32/L frame
 // pairs from *counter; pair_of(pair index, ft) gives the two frames of a pair.
 // While it runs the forward procedure of a task, the warp walks the previous
 // task's traceback one group per chunk (the two tasks' survivors live in the
 // two halves of the warp's scratch), so the traceback's latency hides behind
-// forward work.  surv: per resident warp 2 x wpad_cap x 32 x NW words.
+// forward work.  surv: per resident warp 2 x wpad_cap x 32 x SW words.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT, typename PairOf>
 __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks, uint32_t *surv_all,
                                                   int32_t wpad_cap, int *status, PairOf &&pair_of) {
     constexpr int PPW = 32 / L;
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
-    constexpr int NW = Cfg::NW;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW, Cfg::EMB>;
-    // Two traceback records per thread when they fit the static shared
-    // memory: the forward pass writes the next pair's record in place while
-    // the hook walks the previous one, so neither occupies registers.
-    constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
-    constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
-    __shared__ TbState tbs[NREC][NT];
-    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
+    constexpr int SW = Cfg::SW;
+    using Sm = PersistentSmem<K, BETA, GENS, L, RADIX4, NT>;
+    using Tb = typename Sm::Tb;
+    constexpr int NREC = Sm::NREC;
+    extern __shared__ __align__(16) uint4 vd_dyn_smem[];
+    auto stg = reinterpret_cast<uint32_t (*)[Tb::STAGE_WORDS]>(vd_dyn_smem);
+    auto tbs = reinterpret_cast<TbState (*)[NT]>(reinterpret_cast<unsigned char *>(vd_dyn_smem) + Sm::STG_BYTES);
     const int wlane = (int)(threadIdx.x & 31u);
     const int group = wlane / L;
     const int lane = wlane % L;
     const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
     const int grp_base = wlane & ~(L - 1);
     const int64_t gwarp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    const size_t buf_words = (size_t)wpad_cap * 32u * (size_t)NW;
+    const size_t buf_words = (size_t)wpad_cap * 32u * (size_t)SW;
     uint32_t *surv = surv_all + (size_t)gwarp * 2u * buf_words;
     uint32_t *my_stg = stg[threadIdx.x >> 5];
     int cur = 0;   // record of the pair being traced back
@@ -135,19 +152,20 @@ template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
 __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const BatchParams p) {
     constexpr int PPW = 32 / L;
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
-    constexpr int NW = Cfg::NW;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, NW, Cfg::EMB>;
-    constexpr size_t STG_BYTES = (size_t)(NT / 32) * Tb::STAGE_WORDS * 4u;
-    constexpr int NREC = (2 * NT * sizeof(TbState) + STG_BYTES <= 48u * 1024u) ? 2 : 1;
-    __shared__ TbState tbs[NREC][NT];
-    __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
+    constexpr int SW = Cfg::SW;
+    using Sm = PersistentSmem<K, BETA, GENS, L, RADIX4, NT>;
+    using Tb = typename Sm::Tb;
+    constexpr int NREC = Sm::NREC;
+    extern __shared__ __align__(16) uint4 vd_dyn_smem[];
+    auto stg = reinterpret_cast<uint32_t (*)[Tb::STAGE_WORDS]>(vd_dyn_smem);
+    auto tbs = reinterpret_cast<TbState (*)[NT]>(reinterpret_cast<unsigned char *>(vd_dyn_smem) + Sm::STG_BYTES);
     const int wlane = (int)(threadIdx.x & 31u);
     const int group = wlane / L;
     const int lane = wlane % L;
     const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (wlane & ~(L - 1)));
     const int grp_base = wlane & ~(L - 1);
     const int64_t gwarp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    const size_t buf_words = (size_t)p.wpad_cap * 32u * (size_t)NW;
+    const size_t buf_words = (size_t)p.wpad_cap * 32u * (size_t)SW;
     uint32_t *surv = p.surv + (size_t)gwarp * 2u * buf_words;
     uint32_t *my_stg = stg[threadIdx.x >> 5];
     int cur = 0;   // record of the pair being traced back

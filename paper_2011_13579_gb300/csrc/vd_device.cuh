@@ -20,17 +20,20 @@
 //     ties included, as Algorithm 1's strict ">" gives) is bit 15 / bit 31 of
 //     the 32-bit sum  c_odd - c_even + 0x8000 (per half), which one 3-input
 //     integer add computes without carries crossing the halves.
-//   * embedded form (radix-2 K=7): a half holds 4 m + j, where the two low
-//     bits j are the decisions of the current stage pair along the state's
-//     survivor.  The odd candidate of stage k of the pair carries + 2^k, so
-//     the max itself sets bit k exactly when the odd predecessor wins or ties
-//     and carries the winner's lower bit along; the fields are stored and
-//     cleared after the pair.  With the scale the bound becomes
-//     4 (F + 2S + (N+1) B) + 3 <= 65535 (unsigned halves), N = 18 for K=7.
-//     Its normalisation is folded into the branch metrics of the next stage
-//     (every candidate gets + 4(F+S) - ref) and needs no clamp: only states
-//     not yet reachable from a head-start state 0 fall below the reference,
-//     for fewer than K-1 stages, and F >= (3(K-1)+1) B keeps them >= 0.
+//   * embedded form (radix-2 K=7): a half holds 8 m + j, where the three
+//     low bits j are the decisions of the current group of three stages
+//     along the state's survivor.  The odd candidate of stage k of the group
+//     carries + 2^k, so the max itself sets bit k exactly when the odd
+//     predecessor wins or ties and carries the winner's lower bits along;
+//     the fields are stored and cleared after the group.  Every chunk of
+//     U = 6 stages starts by subtracting the minimum over the states down to
+//     the floor F = U B (folded into the branch metrics of its first stage,
+//     no clamp), and a frame that starts from the reset state gets the
+//     code's tight head start HT (Code::HT) instead of S; the bound is
+//     8 (F + HT + (2 (K-2) + U) B) + 7 <= 65535 (see StreamCfg).  A two-stage
+//     form (4 m + j, state 0 as the reference every N = 18 stages, bound
+//     4 (F + 2S + (N+1) B) + 3 <= 65535) serves codes where three stages do
+//     not fit.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -112,6 +115,29 @@ struct Code {
     static constexpr int B = BETA * 127;         // |branch metric| bound for int8 LLRs
     static constexpr int RANGE = 2 * B;          // delta_max - delta_min
     static constexpr int S = (K - 1) * RANGE + 1;  // head start / normalisation offset
+
+    // Tight head start.  A path from a start state D != 0 can meet the path
+    // from state 0 at a state j within K-1 stages only if both carry the
+    // same inputs (j holds them), so their outputs differ only through the
+    // bits of D still in the register: at the i-th stage the register
+    // differs by D >> (i-1).  DMAX is the largest number of differing output
+    // bits over all D, and 2 * 127 per differing bit bounds the lead such a
+    // path can take over the path from state 0.  The second term keeps every
+    // state reachable from state 0 ahead of every state that is not, until
+    // all are reachable (K-1 stages), so an argmax never picks the latter.
+    __host__ __device__ static constexpr int dmax() {
+        int best = 0;
+        for (uint32_t D = 1; D < (uint32_t)NS; ++D) {
+            int d = 0;
+            for (int i = 0; i < NB; ++i)
+                for (int b = 0; b < BETA; ++b) d += parity32(gen_of(GENS, b) & (D >> i));
+            best = d > best ? d : best;
+        }
+        return best;
+    }
+    static constexpr int DMAX = dmax();
+    static constexpr int HT = (2 * 127 * DMAX > 2 * (NB - 1) * B ? 2 * 127 * DMAX : 2 * (NB - 1) * B) + 1;
+    static_assert(HT <= S, "the tight head start never exceeds the loose one");
 
     // output pattern (beta bits, bit b = output b) of the branch leaving state s on input u
     __host__ __device__ static constexpr uint32_t out(uint32_t s, int u) {

@@ -20,7 +20,7 @@ constexpr int kThreads = 128;
 // Geometry of one instantiation, for scratch sizing on the host.
 struct KernelGeom {
     int U;       // stages per chunk
-    int NW;      // survivor words per thread per stage
+    int NW;      // survivor scratch words per thread per stage (StreamCfg::SW)
 };
 
 // Returns cudaErrorInvalidValue if (kind, lanes, radix4) has no instantiation.

@@ -29,10 +29,12 @@
 //     word (r >> 5) holds register r of the lane (r & 15 at bit 16h for a
 //     lane with 16 registers; frame h = 0, 1);
 //   * radix-2 K=7 embeds the decisions in the metrics instead (see
-//     StreamCfg::EMB and forward_pair): each stage pair leaves one record of
-//     2-bit fields per register, word r >> 3 at bits 2 (r & 7) + 16h, whose
-//     bit 1 is the register's decision at the pair's second stage and bit 0
-//     the decision at the first stage of the register that won;
+//     StreamCfg::ES and forward_pair): each group of three stages leaves one
+//     record of 4-bit fields per register, word r >> 2 at bits 4 (r & 3) +
+//     16h, whose bit 2 is the register's decision at the record's last
+//     stage, bit 1 the decision at the stage before of the register it came
+//     from, and bit 0 the decision one stage earlier along the same
+//     survivor (the two-stage form, ES = 2, has 2-bit fields, word r >> 3);
 //   * radix-4: stages are taken in pairs (t-1, t).  The metrics are two
 //     radix-2 steps (grouping the four candidates of a right state by their
 //     middle state, as Eq. radix4:PM allows, gives exactly the same integers
@@ -58,7 +60,7 @@ struct StreamParams {
     uint32_t flags;         // bit0: terminated, bit1: start state unknown
     int32_t wpad_max;       // padded frame length the scratch of one warp holds
     uint32_t *out;          // packed decoded bits, LSB-first
-    uint32_t *surv;         // survivor scratch: wpad_max x 32 x NW words per warp
+    uint32_t *surv;         // survivor scratch: wpad_max x 32 x SW words per warp
     int32_t *pm_out;        // optional [n_win][2^(K-1)] canonical final metrics
     int *status;            // device status word (bit 0: a frame pair exceeded the scratch)
     int *counter;           // persistent form: task counter, zero at launch
@@ -115,30 +117,64 @@ struct StreamCfg {
     static constexpr int WPF = NR >= 32 ? NR / 32 : 1;// survivor words per frame per lane per stage
     static constexpr int NACC = NR >= 16 ? NR / 16 : 1;
     // Embedded decisions (radix-2, when the range allows): metrics are kept
-    // as 4 m + j, the two low bits j of each half carrying the decisions of
-    // the current stage pair; see forward_pair.  Longest normalisation period
-    // (stages) that keeps 4 (F + 2S + (N+1) B) + 3 within 16 unsigned bits:
+    // as 2^ES m + j, the ES low bits j of each half carrying the decisions of
+    // the current record of ES stages; see forward_pair.  ES = 0: one
+    // decision word per stage instead.
+    //
+    // ES = 3 (records of three stages, metric scale 8): every chunk starts by
+    // subtracting the minimum over the states (folded into its first stage)
+    // down to the floor F3 = U B, and a frame that starts from the reset
+    // state gets the tight head start C::HT.  Bounds on m (per half):
+    //   * steady state: after a normalisation m is in [F3, F3 + SP] with
+    //     SP = (K-1)(delta_max - delta_min) the spread of all metrics once
+    //     every state is reachable; a chunk moves m by at most U B either way,
+    //     so m stays in [0, F3 + SP + U B];
+    //   * after a head start with t < K-1 stages left in its chunk, states
+    //     not yet reachable from state 0 lie within t B of the old floor and
+    //     the others within t B of it plus HT, so the next normalisation
+    //     leaves m <= F3 + HT + 2 t B, and the next chunk adds U B.
+    // The largest 8 m + 7 must stay within 16 unsigned bits.
+    static constexpr int F3 = U * C::B;
+    static constexpr int TMAX = U < NB - 1 ? U : NB - 1;
+    static constexpr int TOP3_STEADY = 2 * NB * C::B + U * C::B;
+    static constexpr int TOP3_RESET = C::HT + (2 * TMAX + U) * C::B;
+    static constexpr int TOP3 = TOP3_STEADY > TOP3_RESET ? TOP3_STEADY : TOP3_RESET;
+    static constexpr bool ES3_OK = !RADIX4 && NB % 3 == 0 && U % 3 == 0 && NR % 4 == 0 &&
+                                   8 * (F3 + TOP3) + 7 <= 65535;
+    // ES = 2 (stage pairs, scale 4): state 0 is the reference every
+    // NORM_CHUNKS chunks with the loose head start C::S.  Longest
+    // normalisation period (stages) that keeps 4 (F + 2S + (N+1) B) + 3
+    // within 16 unsigned bits:
     static constexpr int NMAX_EMB = (16383 - 2 * C::S) / (2 * C::B) - 1;
-    static constexpr bool EMB = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
-    static constexpr int SC = EMB ? 4 : 1;            // metric scale
-    static constexpr int NWE = NR / 8;                // record words per lane per stage pair (EMB)
+    static constexpr bool ES2_OK = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
+    static constexpr int ES = ES3_OK ? 3 : (ES2_OK ? 2 : 0);
+    static constexpr bool EMB = ES != 0;
+    static constexpr int SC = 1 << ES;                // metric scale
+    static constexpr int FW = ES == 3 ? 4 : 2;        // record field width (bits)
+    static constexpr int RPW = 16 / FW;               // registers per record word (per half)
+    static constexpr int NWE = NR / RPW;              // record words per lane per record (EMB)
+    static constexpr int HS = ES == 3 ? C::HT : C::S; // head start of a frame from the reset state
+    // scratch words per lane per stage (records of ES stages, or words per stage)
+    static constexpr int SW = EMB ? ((NWE + ES - 1) / ES > NW ? (NWE + ES - 1) / ES : NW) : NW;
     // normalisation period (multiple of U), see the header of vd_device.cuh
-    static constexpr int NMAX = EMB ? NMAX_EMB : (32767 - 2 * C::S) / (2 * C::B) - 1;
-    static constexpr int NORM_CHUNKS = (NMAX / U) > 0 ? (NMAX / U) : 1;
-    static constexpr int F = (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
+    static constexpr int NMAX = ES == 2 ? NMAX_EMB : (32767 - 2 * C::S) / (2 * C::B) - 1;
+    static constexpr int NORM_CHUNKS = ES == 3 ? 1 : ((NMAX / U) > 0 ? (NMAX / U) : 1);
+    static constexpr int F = ES == 3 ? F3 : (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
     static_assert(NS % L == 0 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
     static_assert(NR >= 2, "at least one butterfly per lane");
     static_assert(!RADIX4 || NB % 2 == 0, "radix-4 pairs need an even rotation period");
-    static_assert(NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
-    static_assert(EMB ? 4 * (F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B) + 3 <= 65535
-                      : F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767,
+    static_assert(ES == 3 || NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
+    static_assert(ES == 3 ? 8 * (F + TOP3) + 7 <= 65535
+                  : ES == 2 ? 4 * (F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B) + 3 <= 65535
+                            : F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767,
                   "metric range");
-    static_assert(!EMB || NWE * 16 <= 32 * NW, "a stage pair's records fit the per-stage scratch");
-    // The embedded form normalises without a clamp.  Below the reference
+    static_assert(!EMB || NWE * 32 <= 32 * ES * SW, "a record fits the scratch of its ES stages");
+    // The ES = 2 form normalises without a clamp.  Below the reference
     // only states not yet reachable from a head-start state 0 can fall (for
     // fewer than K-1 stages), by at most 2(K-1)B before and (K-1)B + B after
     // a normalisation, so a floor F >= (3(K-1) + 1) B keeps them >= 0.
-    static_assert(!EMB || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
+    static_assert(ES != 2 || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
+    static_assert(ES != 3 || F >= U * C::B, "min-normalisation floor covers a chunk's fall");
 };
 
 template <typename Fn, int... S>
@@ -216,6 +252,26 @@ __host__ __device__ constexpr uint32_t bitk_mask(int k) {
          : k == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
+// Per-half minimum of N packed registers: a tree of three-input minima.
+template <int N>
+__device__ __forceinline__ uint32_t min_tree(const uint32_t (&v)[N]) {
+    if constexpr (N == 1) {
+        return v[0];
+    } else if constexpr (N == 2) {
+        return min_u16x2(v[0], v[1]);
+    } else {
+        constexpr int M = (N + 2) / 3;
+        uint32_t w[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (3 * i + 2 < N) w[i] = __vimin3_u16x2(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+            else if (3 * i + 1 < N) w[i] = min_u16x2(v[3 * i], v[3 * i + 1]);
+            else w[i] = v[3 * i];
+        }
+        return min_tree<M>(w);
+    }
+}
+
 // ------------------------------------------------------------ traceback
 //
 // Backward procedure (Algorithm 2) for one pair of frames, resumable: it walks
@@ -289,28 +345,32 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int K, int L, bool RADIX4, int NR, int NW, bool EMB = false>
+template <int K, int L, bool RADIX4, int NR, int NW, int ES = 0>
 struct Traceback {
     static constexpr int NB = K - 1;
     static constexpr int G = NB;                 // stages per group
     static constexpr int LR = ilog2(NR);
     static constexpr int WPF = NR >= 32 ? NR / 32 : 1;
+    static constexpr bool EMB = ES != 0;
+    static constexpr int FW = ES == 3 ? 4 : 2;   // record field width (bits)
+    static constexpr int RPW = 16 / FW;          // registers per record word (per half)
     // survivor records: one per stage (NW words per lane), or with embedded
-    // decisions one per stage pair (NR / 8 words per lane, 2-bit fields)
-    static constexpr int REC = EMB ? G / 2 : G;  // records per group
-    static constexpr int RW = EMB ? NR / 8 : NW; // words per record and lane
+    // decisions one per ES stages (NR / RPW words per lane, FW-bit fields)
+    static constexpr int REC = EMB ? G / ES : G; // records per group
+    static constexpr int RW = EMB ? NR / RPW : NW;   // words per record and lane
     static constexpr int SLOT_WORDS = REC * 32 * RW;
     static constexpr int STAGE_WORDS = 2 * SLOT_WORDS;   // per warp
-    static_assert(!EMB || (G % 2 == 0 && !RADIX4), "embedded decisions: radix-2, stage pairs");
+    static_assert(!EMB || (G % ES == 0 && !RADIX4), "embedded decisions: radix-2, whole records per group");
 
     // Copies the records of stages t0, t0-1, .., t0-G+1 (those >= tau_store) to a slot.
     __device__ static void issue(const TbState &s, int t0, uint32_t *slot, int wlane) {
 #pragma unroll
         for (int g = 0; g < REC; ++g) {
-            const int t = t0 - (EMB ? 2 * g : g);   // EMB: the second stage of a pair
+            const int t = t0 - (EMB ? ES * g : g);   // EMB: the last stage of a record
             if (t >= s.tau_store) {
                 uint32_t *dst = slot + (g * 32 + wlane) * RW;
-                const uint32_t *src = s.surv() + (size_t)(EMB ? (t >> 1) : t) * 32 * RW;
+                // this lane's words of scratch row t / ES (EMB) or t
+                const uint32_t *src = s.surv() + (size_t)(EMB ? (t / ES) : t) * 32 * RW;
                 if constexpr (RW == 1) {
                     cp_async_bytes4(dst, src);
                 } else if constexpr (RW == 2) {
@@ -335,7 +395,7 @@ struct Traceback {
 
     // A group walk in pieces: open() before the group's first record,
     // walk<j>() per record, close() after the last.
-    static constexpr int STEPS = EMB ? G / 2 : (RADIX4 ? G / 2 : G);   // walk<> calls per group
+    static constexpr int STEPS = EMB ? G / ES : (RADIX4 ? G / 2 : G);   // walk<> calls per group
     struct Live {
         uint32_t R[2];           // traceback registers of both frames
         const uint32_t *slot;    // staging slot of the group
@@ -389,21 +449,22 @@ struct Traceback {
             else return x;
         };
         if constexpr (EMB) {
-            // pair record of stages (t-1, t): register R's 2-bit field holds
-            // the decision of R at stage t (bit 1) and the decision at stage
-            // t-1 of the register it came from (bit 0).  The phases of t and
-            // t-1 are adjacent (t's is odd), so one rotation puts both bits in
-            // place and one select replaces both bits of R.
-            constexpr int ph1 = ((NB - 1 - 2 * j) % NB + NB) % NB;
-            constexpr int ph0 = ph1 - 1;
-            static_assert(ph1 >= 1, "the second stage of a pair has an odd phase");
-            constexpr uint32_t m = 3u << ph0;
+            // record of stages (t-ES+1 .. t): register R's field holds the
+            // decision of R at stage t (bit ES-1), the decision at stage t-1
+            // of the register it came from (bit ES-2), and so on.  The phases
+            // of the record's stages are adjacent (a group starts at phase 0
+            // and holds whole records), so one rotation puts every bit in
+            // place and one select replaces those bits of R.
+            constexpr int phh = ((NB - 1 - ES * j) % NB + NB) % NB;   // phase of stage t
+            constexpr int ph0 = phh - (ES - 1);
+            static_assert(ph0 >= 0, "a record's phases do not wrap");
+            constexpr uint32_t m = ((1u << ES) - 1u) << ph0;
             const uint32_t *rec = v.slot + (j * 32 + wlane) * RW;   // this lane's record
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t R = v.R[h];
-                const uint32_t word = rec[(R >> 3) & (uint32_t)(RW - 1)];   // the word holding R
-                const uint32_t sh = 2u * (R & 7u) + 16u * (uint32_t)h;
+                const uint32_t word = rec[(R / RPW) & (uint32_t)(RW - 1)];   // the word holding R
+                const uint32_t sh = (uint32_t)FW * (R & (uint32_t)(RPW - 1)) + 16u * (uint32_t)h;
                 const uint32_t t = owner(__funnelshift_r(word, word, sh - (uint32_t)ph0), R);
                 v.R[h] = (R & ~m) | (t & m);
             }
@@ -502,7 +563,7 @@ struct Traceback {
 
 // Forward procedure (Algorithm 1) and survivor storage for one pair of frames.
 // Called by one group of L lanes; surv is the frame pair's survivor buffer in
-// this warp's scratch (wpad_cap stages x 32 lanes x NW words); wlane is the
+// this warp's scratch (wpad_cap stages x 32 lanes x SW words); wlane is the
 // lane in the warp.  hook(integral_constant<int, S>) runs after stage S of
 // every chunk of U stages (the persistent kernels walk a previous pair's
 // traceback there, a group per K-1 stages).  On return tb
@@ -519,8 +580,11 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     constexpr bool EMB = Cfg::EMB;
     constexpr uint32_t LV = C::lv(), MV = C::mv();
     constexpr uint32_t F2 = (uint32_t)(Cfg::SC * Cfg::F) * 0x00010001u;
-    constexpr uint32_t S2 = (uint32_t)(Cfg::SC * C::S) * 0x00010001u;
-    constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::F + C::S)) * 0x00010001u;  // all-equal start, normalised state 0
+    constexpr uint32_t S2 = (uint32_t)(Cfg::SC * Cfg::HS) * 0x00010001u;   // head start
+    // all-equal start and normalisation target: state 0 at F + S (ES = 0, 2),
+    // or the minimum over the states at the floor F (ES = 3)
+    constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::ES == 3 ? Cfg::F : Cfg::F + C::S)) * 0x00010001u;
+    constexpr int ES = Cfg::ES, RPW = Cfg::RPW, FW = Cfg::FW;
 
     // ---------------------------------------------------------- frame plan
     int64_t fa[2], fb[2], fo[2], fe[2];
@@ -594,39 +658,33 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const int32_t hi0 = valid[0] ? (int32_t)W[0] * BETA : 0, hi1 = valid[1] ? (int32_t)W[1] * BETA : 0;
     int32_t vb0 = -tau0[0] * BETA, vb1 = -tau0[1] * BETA;   // offset of the chunk being fetched
 
-    // EMB: the record of stage pair (tau - 1, tau), stored at pair index tau / 2
-    auto store_rec = [&](int tau, const uint32_t (&rec)[NWE]) {
-        uint32_t *dst = surv + ((size_t)(tau >> 1) * 32 + wlane) * NWE;
-        if constexpr (NWE == 1) {
-            *dst = rec[0];
-        } else if constexpr (NWE == 2) {
-            *reinterpret_cast<uint2 *>(dst) = make_uint2(rec[0], rec[1]);
+    // Scratch rows (a record, or a stage's decision words) of W words per
+    // lane, lane-major: row r of lane l starts at word (32 r + l) W.
+    // EMB: the record of stages (tau - ES + 1 .. tau) is row tau / ES.
+    auto store_row = [&](size_t row, auto const &v) {
+        constexpr int W = (int)(sizeof(v) / sizeof(uint32_t));
+        uint32_t *dst = surv + (row * 32 + (size_t)wlane) * W;
+        if constexpr (W == 1) {
+            *dst = v[0];
+        } else if constexpr (W == 2) {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
         } else {
 #pragma unroll
-            for (int i = 0; i < NWE; i += 4)
-                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(rec[i], rec[i + 1], rec[i + 2], rec[i + 3]);
+            for (int i = 0; i < W; i += 4)
+                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
     };
-    auto store_words = [&](int tau, const uint32_t (&wd)[NW]) {
-        uint32_t *dst = surv + ((size_t)tau * 32 + wlane) * NW;
-        if constexpr (NW == 1) {
-            *dst = wd[0];
-        } else if constexpr (NW == 2) {
-            *reinterpret_cast<uint2 *>(dst) = make_uint2(wd[0], wd[1]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < NW; i += 4)
-                *reinterpret_cast<uint4 *>(dst + i) = make_uint4(wd[i], wd[i + 1], wd[i + 2], wd[i + 3]);
-        }
-    };
+    auto store_rec = [&](int tau, const uint32_t (&rec)[NWE]) { store_row((size_t)(tau / (ES > 0 ? ES : 1)), rec); };
+    auto store_words = [&](int tau, const uint32_t (&wd)[NW]) { store_row((size_t)tau, wd); };
 
     // runtime +1 / -1 for the FMA-pipe multiply-adds (blocks are one-dimensional)
     const uint32_t one = threadIdx.y + 1u;
     const uint32_t m1 = 0u - one;
-    const uint32_t four = one << 2;
+    const uint32_t fwmul = one << FW;   // 2^FW: shifts a record word by one field
     constexpr bool COROLLARY = LV == (1u << BETA) - 1u && MV == (1u << BETA) - 1u;
 
     const int nchunks = Wpad / U;
+    uint32_t pmin = SEED0;   // ES = 3: per-half minimum metric at the end of the last chunk
     ChunkRaw<UW> nx0, nx1;
     if (nchunks > 0) {
         fetch_chunk<UW>(fbase0, vb0, hi0, nx0);
@@ -647,13 +705,18 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             finish_chunk<UW>(fbase1, cb1, hi1, cur1, cw1);
         }
         uint32_t W1[NW];   // radix-4: decisions of the first stage of a pair
-        // embedded form: the normalisation of every NORM_CHUNKS-th chunk
-        // boundary is folded into the branch metrics of the chunk's first
-        // stage (adding tn to every candidate shifts every new metric by tn,
-        // as normalising before the stage would).  tn = 4(F+S) - (metric of
-        // state 0), or 0 between normalisations.
+        // embedded form: the normalisation at a chunk boundary is folded
+        // into the branch metrics of the chunk's first stage (adding tn to
+        // every candidate shifts every new metric by tn, as normalising
+        // before the stage would).  ES = 2: tn = 4(F+S) - (metric of state 0)
+        // every NORM_CHUNKS chunks, else 0; ES = 3: tn = 8F - (minimum over
+        // the states, taken at the end of the previous chunk) every chunk.
         uint32_t tn = 0, tn1 = 0, tn2 = 0;
-        if constexpr (EMB) {
+        if constexpr (ES == 3) {
+            tn = sub_s16x2(SEED0, pmin);
+            tn1 = add_u16x2(tn, 0x00010001u);   // -x + tn = ~x + tn1
+            tn2 = add_u16x2(tn, 0x00020002u);   // -x + 1 + tn (odd candidates of stage 0)
+        } else if constexpr (EMB) {
             uint32_t ref = P[0];
             if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
             tn = (c > 0 && c % Cfg::NORM_CHUNKS == 0) ? sub_s16x2(SEED0, ref) : 0u;
@@ -709,17 +772,22 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 }
             }
             if constexpr (EMB) {
-                // ---- embedded decisions.  A metric half is 4 m + j: m the
-                // path metric (Eq. PM) and j < 4 the decisions (Eq. SP0) of
-                // the current stage pair along the state's survivor.  Odd
-                // candidates carry + 2^k at the pair's stage k, so the max
-                // itself records "the odd predecessor wins or ties" in bit k
-                // (|4 dm| >= 4 exceeds any j + 2^k difference, and on a tie
-                // the odd candidate is larger by 2^k + j_odd - j_even > 0),
-                // and the winner's own bits below k (its decision at stage
-                // k - 1) travel with it.  After the second stage the fields
-                // are stored and cleared: no per-state decision arithmetic.
-                constexpr uint32_t OFF = (S & 1) ? 0x00020002u : 0x00010001u;
+                // ---- embedded decisions.  A metric half is 2^ES m + j: m the
+                // path metric (Eq. PM) and j < 2^ES the decisions (Eq. SP0)
+                // of the current record of ES stages along the state's
+                // survivor.  Odd candidates carry + 2^k at the record's stage
+                // k, so the max itself records "the odd predecessor wins or
+                // ties" in bit k: with j_even, j_odd < 2^k a tie leaves the
+                // odd candidate larger by 2^k + j_odd - j_even > 0, and a
+                // metric difference of one (2^ES in these units) outweighs
+                // 2^k + j_odd - j_even <= 2^(k+1) - 1 <= 2^ES - 1.  The
+                // winner's own bits below k (its decisions at the record's
+                // earlier stages) travel with it.  After the record's last
+                // stage the fields are stored and cleared: no per-state
+                // decision arithmetic.
+                constexpr int KS = S % ES;   // stage within the record
+                constexpr uint32_t OFF = 0x00010001u << KS;
+                constexpr uint32_t SCM = (0xFFFFu & ~(uint32_t)(Cfg::SC - 1)) * 0x00010001u;
                 uint32_t A4[1 << BETA], A4o[1 << BETA];
                 if constexpr (COROLLARY) {
                     // complement patterns have the negated metric: scale half
@@ -727,7 +795,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     constexpr int FULL = (1 << BETA) - 1;
 #pragma unroll
                     for (int x = 0; x < (1 << (BETA - 1)); ++x) {
-                        const uint32_t a4 = (A[x] << 2) & 0xFFFCFFFCu;   // 4 delta per half
+                        const uint32_t a4 = (A[x] << ES) & SCM;   // 2^ES delta per half
                         const uint32_t n = ~a4;
                         if constexpr (S == 0) {   // with the folded normalisation
                             A4[x] = add_u16x2(a4, tn);
@@ -743,7 +811,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 } else {
 #pragma unroll
                     for (int x = 0; x < (1 << BETA); ++x) {
-                        A4[x] = (A[x] << 2) & 0xFFFCFFFCu;
+                        A4[x] = (A[x] << ES) & SCM;
                         if constexpr (S == 0) A4[x] = add_u16x2(A4[x], tn);
                         A4o[x] = add_u16x2(A4[x], OFF);
                     }
@@ -775,20 +843,31 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
 #pragma unroll
                     for (int r = 0; r < NR; ++r) cross_e(r);
                 }
-                if constexpr (S & 1) {
-                    // record word m: register 8m + i at bits 2i (frame 0) and
-                    // 16 + 2i (frame 1); fields cleared, half by a select
-                    // (ALU) and half by a multiply-add (FMA pipe)
+                if constexpr (KS == ES - 1) {
+                    // record word m: register RPW m + i at bits FW i (frame 0)
+                    // and 16 + FW i (frame 1); fields cleared, half by a
+                    // select (ALU) and half by a multiply-add (FMA pipe)
+                    constexpr uint32_t FM = ((1u << ES) - 1u) * 0x00010001u;
+                    if constexpr (ES == 3 && S == U - 1) {
+                        // the minimum over the states for the next chunk's
+                        // normalisation: min of 8 m + j, fields masked off
+                        pmin = min_tree<NR>(P) & ~FM;
+                        if constexpr (L > 1) {
+#pragma unroll
+                            for (int m = 1; m < L; m <<= 1)
+                                pmin = min_u16x2(pmin, __shfl_xor_sync(gmask, pmin, m));
+                        }
+                    }
                     uint32_t rec[NWE];
 #pragma unroll
                     for (int m = 0; m < NWE; ++m) {
                         uint32_t acc = 0;
 #pragma unroll
-                        for (int i = 7; i >= 0; --i) {
-                            const int r = 8 * m + i;
-                            const uint32_t d = P[r] & 0x00030003u;
-                            P[r] = (i & 1) ? imad(d, m1, P[r]) : (P[r] & ~0x00030003u);
-                            acc = (i == 7) ? d : imad(acc, four, d);
+                        for (int i = RPW - 1; i >= 0; --i) {
+                            const int r = RPW * m + i;
+                            const uint32_t d = P[r] & FM;
+                            P[r] = (i & 1) ? imad(d, m1, P[r]) : (P[r] & ~FM);
+                            acc = (i == RPW - 1) ? d : imad(acc, fwmul, d);
                         }
                         rec[m] = acc;
                     }
@@ -1042,7 +1121,7 @@ template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, int NT>
 __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     constexpr int NS = 1 << (K - 1);
     using Cfg = StreamCfg<K, BETA, GENS, L, RADIX4>;
-    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW, Cfg::EMB>;
+    using Tb = Traceback<K, L, RADIX4, Cfg::NR, Cfg::NW, Cfg::ES>;
     __shared__ TbState tbs[NT];
     __shared__ __align__(16) uint32_t stg[NT / 32][Tb::STAGE_WORDS];
     const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -1059,7 +1138,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
         ft[h] = frame_task(p.llr, p.out, p.pm_out ? p.pm_out + s * NS : nullptr, s, p.n_win,
                            p.n_info, p.T, p.f, p.v, p.flags);
     }
-    uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::NW;
+    uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::SW;
     TbState &st = tbs[threadIdx.x];
     forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
                                            st, [](auto) {});

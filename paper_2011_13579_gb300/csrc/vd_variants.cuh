@@ -3,6 +3,7 @@
 // the kernel definitions; the dispatch unit only needs the declarations, so
 // the heavy kernels of different variants compile in parallel.
 #pragma once
+#include <atomic>
 #include "vd_launch.h"
 
 namespace vd {
@@ -17,30 +18,76 @@ cudaError_t launch_stream_v(const StreamParams &p, int64_t blocks, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the persistent kernels (PersistentSmem).  A
+// block may use more than 48 KB only after the kernel opts in, once per
+// device (the attribute belongs to the kernel in that device's context);
+// the flags are per kernel instantiation, devices 0..63.
+template <int K, bool R4, int L>
+constexpr size_t persistent_smem_bytes() {
+    return PersistentSmem<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>::BYTES;
+}
+
+template <typename Kern>
+cudaError_t opt_in_smem(Kern kern, size_t bytes, std::atomic<uint64_t> &done) {
+    if (bytes <= 48u * 1024u) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+template <int K, bool R4, int L>
+cudaError_t batch_smem_opt_in() {
+    static std::atomic<uint64_t> done{0};
+    return opt_in_smem(batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>,
+                       persistent_smem_bytes<K, R4, L>(), done);
+}
+
+template <int K, bool R4, int L>
+cudaError_t stream_persistent_smem_opt_in() {
+    static std::atomic<uint64_t> done{0};
+    return opt_in_smem(stream_persistent_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>,
+                       persistent_smem_bytes<K, R4, L>(), done);
+}
+
 template <int K, bool R4, int L>
 cudaError_t launch_batch_v(const BatchParams &p, int64_t blocks, cudaStream_t st) {
-    batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(p);
+    const cudaError_t e = batch_smem_opt_in<K, R4, L>();
+    if (e != cudaSuccess) return e;
+    batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>
+        <<<(unsigned)blocks, kThreads, persistent_smem_bytes<K, R4, L>(), st>>>(p);
     return cudaGetLastError();
 }
 
 template <int K, bool R4, int L>
 cudaError_t occupancy_v(int *blocks_per_sm) {
+    const cudaError_t e = batch_smem_opt_in<K, R4, L>();
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>, kThreads, 0);
+        blocks_per_sm, batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>, kThreads,
+        persistent_smem_bytes<K, R4, L>());
 }
 
 template <int K, bool R4, int L>
 cudaError_t launch_stream_persistent_v(const StreamParams &p, int64_t blocks, cudaStream_t st) {
+    const cudaError_t e = stream_persistent_smem_opt_in<K, R4, L>();
+    if (e != cudaSuccess) return e;
     stream_persistent_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>
-        <<<(unsigned)blocks, kThreads, 0, st>>>(p);
+        <<<(unsigned)blocks, kThreads, persistent_smem_bytes<K, R4, L>(), st>>>(p);
     return cudaGetLastError();
 }
 
 template <int K, bool R4, int L>
 cudaError_t occupancy_stream_v(int *blocks_per_sm) {
+    const cudaError_t e = stream_persistent_smem_opt_in<K, R4, L>();
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         blocks_per_sm, stream_persistent_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>,
-        kThreads, 0);
+        kThreads, persistent_smem_bytes<K, R4, L>());
 }
 
 // The instantiations that exist (each compiled in one inst_*.cu unit).

@@ -207,6 +207,42 @@ def test_head_start_near_normalisation_k7(kind):
             check(gw, gpm, ow, opm, 7, n, f, v, T, term, False)
 
 
+def _path_outputs(K, gens, s, inputs):
+    """Output bits (stage-major, generator order) of the encoder path that
+    starts in state s (register r = (u << (K-1)) | s, next state
+    (u << (K-2)) | (s >> 1), as in the oracle's trellis)."""
+    out = []
+    for u in inputs:
+        r = (u << (K - 1)) | s
+        out += [bin(g & r).count("1") & 1 for g in gens]
+        s = (u << (K - 2)) | (s >> 1)
+    return out
+
+
+@pytest.mark.parametrize("D", [51, 1, 32, 63])
+def test_head_start_adversarial_k7(D):
+    """The frame that starts from the reset state: its first K-1 stages carry
+    saturated LLRs that match the path from start state D != 0 (zero inputs),
+    so that path leads the path from state 0 with the same inputs by 254 per
+    differing output bit (2540 for D = 51 with the 171/133 code, the largest
+    lead any start state can take).  The oracle starts the other states at
+    -infinity; the GPU's finite head start must keep the path from state 0
+    ahead, which the frame's final canonical metrics show (the decoded bits
+    cannot: both paths carry the same inputs).  The reset stage is swept over
+    every position within a chunk of the kernel's unrolled stages."""
+    K, gens = 7, synth.K7_GENS
+    oc = oracle.Code(K, gens)
+    code = gpu_code(K, gens)
+    lead = np.array(_path_outputs(K, gens, D, [0] * (K - 1)))
+    for n, f, v in [(600 + i, 4096, 6) for i in range(6)] + [(700, 64, v) for v in range(6, 12)]:
+        rng = np.random.Generator(np.random.PCG64(4000 + 17 * D + n + v))
+        q = synth.make_stream(rng, K, gens, n, 2.0, False).s8().copy()
+        q[:2 * (K - 1)] = np.where(lead == 0, 127, -127).astype(np.int8)
+        ow, opm = run_oracle(oc, q.reshape(n, 2).astype(np.int32), n, f, v)
+        gw, gpm = run_gpu(code, q, n, f, v, lanes=1)
+        check(gw, gpm, ow, opm, K, n, f, v, n, False, False)
+
+
 @pytest.mark.parametrize("n,f,v,term", [(1, 32, 8, True), (70, 64, 3, False), (2000, 512, 64, True),
                                         (2049, 1024, 700, False)])
 @pytest.mark.parametrize("kind", ["noisy", "zeros", "erasures"])
