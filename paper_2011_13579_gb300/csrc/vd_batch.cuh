@@ -122,8 +122,9 @@ __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks,
             TbState &next = tbs[cur ^ 1][threadIdx.x];
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, next,
-                [&](auto Sc) {
-                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                [&](auto Sc, int c) {
+                    Tb::template sub<decltype(Sc)::value, Cfg::U>(pend, my_stg, live, wlane, lane, gmask,
+                                                                  grp_base, c);
                 });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             cur ^= 1;
@@ -131,8 +132,9 @@ __device__ __forceinline__ void persistent_decode(int *counter, int64_t n_tasks,
             TbState tb;
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, wpad_cap, wlane, lane, gmask, grp_base, status, tb,
-                [&](auto Sc) {
-                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                [&](auto Sc, int c) {
+                    Tb::template sub<decltype(Sc)::value, Cfg::U>(pend, my_stg, live, wlane, lane, gmask,
+                                                                  grp_base, c);
                 });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             pend = tb;
@@ -195,8 +197,9 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
             TbState &next = tbs[cur ^ 1][threadIdx.x];
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, next,
-                [&](auto Sc) {
-                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                [&](auto Sc, int c) {
+                    Tb::template sub<decltype(Sc)::value, Cfg::U>(pend, my_stg, live, wlane, lane, gmask,
+                                                                  grp_base, c);
                 });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             cur ^= 1;
@@ -204,8 +207,9 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
             TbState tb;
             forward_pair<K, BETA, GENS, L, RADIX4>(
                 ft, surv + (size_t)buf * buf_words, p.wpad_cap, wlane, lane, gmask, grp_base, p.status, tb,
-                [&](auto Sc) {
-                    Tb::template sub<decltype(Sc)::value>(pend, my_stg, live, wlane, lane, gmask, grp_base);
+                [&](auto Sc, int c) {
+                    Tb::template sub<decltype(Sc)::value, Cfg::U>(pend, my_stg, live, wlane, lane, gmask,
+                                                                  grp_base, c);
                 });
             Tb::drain(pend, my_stg, wlane, lane, gmask, grp_base);
             pend = tb;

@@ -45,7 +45,8 @@
 //   * traceback (Algorithm 2) walks groups of K-1 stages whose survivor words
 //     are staged in shared memory; a group's decoded bits are the register
 //     index at the group's start.  The persistent kernels (vd_batch.cuh) run
-//     one pair's traceback a group per chunk of the next pair's forward pass.
+//     one pair's traceback, two groups every second group of stages, during
+//     the next pair's forward pass.
 #pragma once
 #include <utility>
 #include "vd_device.cuh"
@@ -362,8 +363,9 @@ struct Traceback {
     static constexpr int STAGE_WORDS = 2 * SLOT_WORDS;   // per warp
     static_assert(!EMB || (G % ES == 0 && !RADIX4), "embedded decisions: radix-2, whole records per group");
 
-    // Copies the records of stages t0, t0-1, .., t0-G+1 (those >= tau_store) to a slot.
-    __device__ static void issue(const TbState &s, int t0, uint32_t *slot, int wlane) {
+    // Copies the records of stages t0, t0-1, .., t0-G+1 (those >= tau_store)
+    // to a slot (the caller commits the copies as one group).
+    __device__ static void issue_slot(const TbState &s, int t0, uint32_t *slot, int wlane) {
 #pragma unroll
         for (int g = 0; g < REC; ++g) {
             const int t = t0 - (EMB ? ES * g : g);   // EMB: the last stage of a record
@@ -381,6 +383,12 @@ struct Traceback {
                 }
             }
         }
+    }
+
+    // Copies the groups of top stages t0 and t0 - G to slots 0 and 1 as one group of copies.
+    __device__ static void issue_pair(const TbState &s, int t0, uint32_t *stg, int wlane) {
+        issue_slot(s, t0, stg, wlane);
+        issue_slot(s, t0 - G, stg + SLOT_WORDS, wlane);
         cp_async_commit();
     }
 
@@ -389,12 +397,12 @@ struct Traceback {
     // Starts the copies of the first two groups.
     __device__ static void begin(TbState &s, uint32_t *stg, int wlane) {
         s.slot = 0;
-        issue(s, s.t0, stg, wlane);
-        issue(s, s.t0 - G, stg + SLOT_WORDS, wlane);
+        issue_pair(s, s.t0, stg, wlane);
     }
 
-    // A group walk in pieces: open() before the group's first record,
-    // walk<j>() per record, close() after the last.
+    // A step walks the two staged groups: open() before the first group's
+    // first record, walk<j>() per record of each group, close() after the
+    // second group's last record.
     static constexpr int STEPS = EMB ? G / ES : (RADIX4 ? G / 2 : G);   // walk<> calls per group
     struct Live {
         uint32_t R[2];           // traceback registers of both frames
@@ -407,8 +415,8 @@ struct Traceback {
     // runs unconditionally (measured 3% faster than a branch around it).
     __device__ static void open(const TbState &s, const uint32_t *stg, Live &v) {
         v.act = active(s);
-        cp_async_wait<1>();
-        v.slot = stg + (s.slot & 1) * SLOT_WORDS;
+        cp_async_wait<0>();
+        v.slot = stg;
         v.R[0] = s.R[0] & (uint32_t)((1 << NB) - 1);
         v.R[1] = s.R[1] & (uint32_t)((1 << NB) - 1);
     }
@@ -497,22 +505,26 @@ struct Traceback {
         }
     }
 
-    // Emits the group's decoded bits, refills its slot with the group two
-    // ahead and advances.
-    __device__ static void close(TbState &s, uint32_t *stg, const Live &v, int wlane, int lane) {
+    // Emits the two groups' decoded bits, refills both slots with the two
+    // groups after them and advances.  RB: the registers after group A (the
+    // start of group B).
+    __device__ static void close(TbState &s, uint32_t *stg, const Live &v, const uint32_t (&RB)[2], int wlane,
+                                 int lane) {
         if (!v.act) return;
         const int t0 = s.t0;
-        const int tl = t0 - (G - 1);   // lowest stage of the group
-        // Each bit position of R is replaced once per group, so the group's
+        const int tl = t0 - (2 * G - 1);   // lowest stage of group B
+        // Each bit position of R is replaced once per group, so a group's
         // decoded bits (the input bit of each stage's state) are the bits of
-        // R at the start of the group (still in s.R): stage tl + i is bit i.
+        // R at the start of the group: group A's from s.R, group B's from RB;
+        // stage tl + i is bit i of (R_A << G) | R_B.
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int lo = tl > s.tauo[h] ? tl : s.tauo[h];
             const int hi = (t0 + 1) < s.taue[h] ? (t0 + 1) : s.taue[h];
             if (hi > lo) {
                 const int m = hi - lo;
-                const uint64_t bits = (uint64_t)((s.R[h] >> (lo - tl)) & ((1u << m) - 1u));
+                const uint32_t X = ((s.R[h] & (uint32_t)((1 << NB) - 1)) << G) | RB[h];
+                const uint64_t bits = (uint64_t)((X >> (lo - tl)) & ((1u << m) - 1u));
                 uint64_t acc = (s.oacc(h) << m) | bits;
                 int nb = s.onb[h] + m;
                 const int a = lo + s.toff[h];              // stream stage of bit 0
@@ -528,29 +540,39 @@ struct Traceback {
         }
         s.R[0] = v.R[0];
         s.R[1] = v.R[1];
-        // refill the consumed slot with the group two ahead, then advance
-        issue(s, t0 - 2 * G, stg + s.slot * SLOT_WORDS, wlane);
-        s.t0 = t0 - G;
-        s.slot ^= 1;
+        // refill both slots with the next two groups, then advance
+        issue_pair(s, t0 - 2 * G, stg, wlane);
+        s.t0 = t0 - 2 * G;
     }
 
-    // The traceback work that belongs after stage S of a forward chunk
-    // (chunks are a whole number of groups): one group after the group's
-    // last stage.  (Spreading the records over the stages was measured 2%
-    // slower: the forward stages schedule better as whole blocks.)
-    template <int S>
+    // The traceback work that belongs after stage S of chunk c of a forward
+    // pass (chunks of U stages, a whole number of groups): one step (two
+    // groups) after the last stage of every second group, so the state
+    // bookkeeping, the wait and the commit are paid once per two groups.
+    // (Spreading the records over the stages was measured 2% slower: the
+    // forward stages schedule better as whole blocks.)
+    template <int S, int U>
     __device__ static void sub(TbState &s, uint32_t *stg, Live &, int wlane, int lane, unsigned gmask,
-                               int grp_base) {
-        if constexpr (S % G == G - 1) step(s, stg, wlane, lane, gmask, grp_base);
+                               int grp_base, int c) {
+        static_assert(U % G == 0, "chunks hold whole groups");
+        if constexpr (S % G == G - 1) {
+            if ((c * (U / G) + S / G) & 1) step(s, stg, wlane, lane, gmask, grp_base);
+        }
     }
 
-    // Walks one group (if any remains) and refills its slot with the group two ahead.
+    // Walks the two staged groups (those that remain) and refills both slots.
     __device__ static void step(TbState &s, uint32_t *stg, int wlane, int lane, unsigned gmask,
                                 int grp_base) {
         Live v;
         open(s, stg, v);
         static_for<STEPS>([&](auto jc) { walk<decltype(jc)::value>(v, wlane, gmask, grp_base); });
-        close(s, stg, v, wlane, lane);
+        const uint32_t RB[2] = {v.R[0], v.R[1]};
+        const bool act = v.act;
+        v.slot = stg + SLOT_WORDS;
+        v.act = act && s.t0 - G >= s.tau_store;
+        static_for<STEPS>([&](auto jc) { walk<decltype(jc)::value>(v, wlane, gmask, grp_base); });
+        v.act = act;
+        close(s, stg, v, RB, wlane, lane);
     }
 
     // Walks every remaining group and waits for all copies.
@@ -564,9 +586,9 @@ struct Traceback {
 // Forward procedure (Algorithm 1) and survivor storage for one pair of frames.
 // Called by one group of L lanes; surv is the frame pair's survivor buffer in
 // this warp's scratch (wpad_cap stages x 32 lanes x SW words); wlane is the
-// lane in the warp.  hook(integral_constant<int, S>) runs after stage S of
-// every chunk of U stages (the persistent kernels walk a previous pair's
-// traceback there, a group per K-1 stages).  On return tb
+// lane in the warp.  hook(integral_constant<int, S>, c) runs after stage S of
+// every chunk c of U stages (the persistent kernels walk a previous pair's
+// traceback there, two groups of K-1 stages every second group).  On return tb
 // holds the traceback start of this pair; returns false (tb inactive) if the
 // pair does not fit the scratch, which host plans never produce.
 template <int K, int BETA, uint64_t GENS, int L, bool RADIX4, typename Hook>
@@ -873,7 +895,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     }
                     if (tau >= tau_store) store_rec(tau, rec);
                 }
-                hook(Sc);
+                hook(Sc, c);
                 return;
             }
 
@@ -1046,7 +1068,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     store_words(tau - 1, lo_w);
                 }
             }
-            hook(Sc);
+            hook(Sc, c);
         });
 
         // ---- normalisation: subtract state 0's metric, add F+S, clamp at F
@@ -1141,7 +1163,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const StreamParams p) {
     uint32_t *surv = p.surv + (size_t)(gtid >> 5) * (size_t)p.wpad_max * 32u * (size_t)Cfg::SW;
     TbState &st = tbs[threadIdx.x];
     forward_pair<K, BETA, GENS, L, RADIX4>(ft, surv, p.wpad_max, wlane, lane, gmask, grp_base, p.status,
-                                           st, [](auto) {});
+                                           st, [](auto, int) {});
     uint32_t *my_stg = stg[threadIdx.x >> 5];
     if (Tb::active(st)) {
         Tb::begin(st, my_stg, wlane);
