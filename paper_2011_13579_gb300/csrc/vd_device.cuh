@@ -122,9 +122,10 @@ struct Code {
     // bits of D still in the register: at the i-th stage the register
     // differs by D >> (i-1).  DMAX is the largest number of differing output
     // bits over all D, and 2 * 127 per differing bit bounds the lead such a
-    // path can take over the path from state 0.  The second term keeps every
-    // state reachable from state 0 ahead of every state that is not, until
-    // all are reachable (K-1 stages), so an argmax never picks the latter.
+    // path can take over the path from state 0: HT = 254 DMAX + 1 keeps the
+    // path from state 0 strictly ahead wherever the two meet.  (States not
+    // yet reachable from state 0 may still lead their own comparisons in a
+    // frame shorter than K-1 stages; the traceback start leaves them out.)
     __host__ __device__ static constexpr int dmax() {
         int best = 0;
         for (uint32_t D = 1; D < (uint32_t)NS; ++D) {
@@ -136,7 +137,7 @@ struct Code {
         return best;
     }
     static constexpr int DMAX = dmax();
-    static constexpr int HT = (2 * 127 * DMAX > 2 * (NB - 1) * B ? 2 * 127 * DMAX : 2 * (NB - 1) * B) + 1;
+    static constexpr int HT = 2 * 127 * DMAX + 1;
     static_assert(HT <= S, "the tight head start never exceeds the loose one");
 
     // output pattern (beta bits, bit b = output b) of the branch leaving state s on input u

@@ -122,60 +122,64 @@ struct StreamCfg {
     // the current record of ES stages; see forward_pair.  ES = 0: one
     // decision word per stage instead.
     //
-    // ES = 3 (records of three stages, metric scale 8): every chunk starts by
-    // subtracting the minimum over the states (folded into its first stage)
-    // down to the floor F3 = U B, and a frame that starts from the reset
-    // state gets the tight head start C::HT.  Bounds on m (per half):
-    //   * steady state: after a normalisation m is in [F3, F3 + SP] with
+    // Min-normalised forms (MINNORM; records of ES = 3 stages, scale 8, or
+    // ES = 2, scale 4): every chunk starts by subtracting the minimum over
+    // the states (folded into its first stage) down to the floor FM = U B,
+    // and a frame that starts from the reset state gets the exact head start
+    // C::HT.  Bounds on m (per half):
+    //   * steady state: after a normalisation m is in [FM, FM + SP] with
     //     SP = (K-1)(delta_max - delta_min) the spread of all metrics once
     //     every state is reachable; a chunk moves m by at most U B either way,
-    //     so m stays in [0, F3 + SP + U B];
+    //     so m stays in [0, FM + SP + U B];
     //   * after a head start with t < K-1 stages left in its chunk, states
     //     not yet reachable from state 0 lie within t B of the old floor and
     //     the others within t B of it plus HT, so the next normalisation
-    //     leaves m <= F3 + HT + 2 t B, and the next chunk adds U B.
-    // The largest 8 m + 7 must stay within 16 unsigned bits.
-    static constexpr int F3 = U * C::B;
+    //     leaves m <= FM + HT + 2 t B, and the next chunk adds U B.
+    // The largest 2^ES m + 2^ES - 1 must stay within 16 unsigned bits.
+    static constexpr int FM = U * C::B;
     static constexpr int TMAX = U < NB - 1 ? U : NB - 1;
-    static constexpr int TOP3_STEADY = 2 * NB * C::B + U * C::B;
-    static constexpr int TOP3_RESET = C::HT + (2 * TMAX + U) * C::B;
-    static constexpr int TOP3 = TOP3_STEADY > TOP3_RESET ? TOP3_STEADY : TOP3_RESET;
+    static constexpr int TOPM_STEADY = 2 * NB * C::B + U * C::B;
+    static constexpr int TOPM_RESET = C::HT + (2 * TMAX + U) * C::B;
+    static constexpr int TOPM = FM + (TOPM_STEADY > TOPM_RESET ? TOPM_STEADY : TOPM_RESET);
     static constexpr bool ES3_OK = !RADIX4 && NB % 3 == 0 && U % 3 == 0 && NR % 4 == 0 &&
-                                   8 * (F3 + TOP3) + 7 <= 65535;
-    // ES = 2 (stage pairs, scale 4): state 0 is the reference every
-    // NORM_CHUNKS chunks with the loose head start C::S.  Longest
-    // normalisation period (stages) that keeps 4 (F + 2S + (N+1) B) + 3
-    // within 16 unsigned bits:
+                                   8 * TOPM + 7 <= 65535;
+    static constexpr bool ES2M_OK = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && 4 * TOPM + 3 <= 65535;
+    // ES = 2 with state 0 as the reference every NORM_CHUNKS chunks and the
+    // loose head start C::S (for codes whose min-normalised range does not
+    // fit).  Longest normalisation period (stages) that keeps
+    // 4 (F + 2S + (N+1) B) + 3 within 16 unsigned bits:
     static constexpr int NMAX_EMB = (16383 - 2 * C::S) / (2 * C::B) - 1;
     static constexpr bool ES2_OK = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
-    static constexpr int ES = ES3_OK ? 3 : (ES2_OK ? 2 : 0);
+    static constexpr int ES = ES3_OK ? 3 : ((ES2M_OK || ES2_OK) ? 2 : 0);
+    static constexpr bool MINNORM = ES3_OK || ES2M_OK;
     static constexpr bool EMB = ES != 0;
     static constexpr int SC = 1 << ES;                // metric scale
     static constexpr int FW = ES == 3 ? 4 : 2;        // record field width (bits)
     static constexpr int RPW = 16 / FW;               // registers per record word (per half)
     static constexpr int NWE = NR / RPW;              // record words per lane per record (EMB)
-    static constexpr int HS = ES == 3 ? C::HT : C::S; // head start of a frame from the reset state
+    static constexpr int HS = MINNORM ? C::HT : C::S; // head start of a frame from the reset state
     // scratch words per lane per stage (records of ES stages, or words per stage)
     static constexpr int SW = EMB ? ((NWE + ES - 1) / ES > NW ? (NWE + ES - 1) / ES : NW) : NW;
     // normalisation period (multiple of U), see the header of vd_device.cuh
     static constexpr int NMAX = ES == 2 ? NMAX_EMB : (32767 - 2 * C::S) / (2 * C::B) - 1;
-    static constexpr int NORM_CHUNKS = ES == 3 ? 1 : ((NMAX / U) > 0 ? (NMAX / U) : 1);
-    static constexpr int F = ES == 3 ? F3 : (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
+    static constexpr int NORM_CHUNKS = MINNORM ? 1 : ((NMAX / U) > 0 ? (NMAX / U) : 1);
+    static constexpr int F = MINNORM ? FM : (NORM_CHUNKS * U + 1) * C::B;   // floor after normalisation
     static_assert(NS % L == 0 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
     static_assert(NR >= 2, "at least one butterfly per lane");
     static_assert(!RADIX4 || NB % 2 == 0, "radix-4 pairs need an even rotation period");
-    static_assert(ES == 3 || NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
-    static_assert(ES == 3 ? 8 * (F + TOP3) + 7 <= 65535
+    static_assert(MINNORM || NORM_CHUNKS * U <= NMAX, "normalisation period too long for 16-bit metrics");
+    static_assert(MINNORM ? SC * TOPM + SC - 1 <= 65535
                   : ES == 2 ? 4 * (F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B) + 3 <= 65535
                             : F + 2 * C::S + (NORM_CHUNKS * U + 1) * C::B <= 32767,
                   "metric range");
     static_assert(!EMB || NWE * 32 <= 32 * ES * SW, "a record fits the scratch of its ES stages");
-    // The ES = 2 form normalises without a clamp.  Below the reference
-    // only states not yet reachable from a head-start state 0 can fall (for
-    // fewer than K-1 stages), by at most 2(K-1)B before and (K-1)B + B after
-    // a normalisation, so a floor F >= (3(K-1) + 1) B keeps them >= 0.
-    static_assert(ES != 2 || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
-    static_assert(ES != 3 || F >= U * C::B, "min-normalisation floor covers a chunk's fall");
+    // The state-0 ES = 2 form normalises without a clamp.  Below the
+    // reference only states not yet reachable from a head-start state 0 can
+    // fall (for fewer than K-1 stages), by at most 2(K-1)B before and
+    // (K-1)B + B after a normalisation, so a floor F >= (3(K-1) + 1) B keeps
+    // them >= 0.
+    static_assert(MINNORM || ES != 2 || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
+    static_assert(!MINNORM || F >= U * C::B, "min-normalisation floor covers a chunk's fall");
 };
 
 template <typename Fn, int... S>
@@ -605,7 +609,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     constexpr uint32_t S2 = (uint32_t)(Cfg::SC * Cfg::HS) * 0x00010001u;   // head start
     // all-equal start and normalisation target: state 0 at F + S (ES = 0, 2),
     // or the minimum over the states at the floor F (ES = 3)
-    constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::ES == 3 ? Cfg::F : Cfg::F + C::S)) * 0x00010001u;
+    constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::MINNORM ? Cfg::F : Cfg::F + C::S)) * 0x00010001u;
     constexpr int ES = Cfg::ES, RPW = Cfg::RPW, FW = Cfg::FW;
 
     // ---------------------------------------------------------- frame plan
@@ -730,11 +734,12 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
         // embedded form: the normalisation at a chunk boundary is folded
         // into the branch metrics of the chunk's first stage (adding tn to
         // every candidate shifts every new metric by tn, as normalising
-        // before the stage would).  ES = 2: tn = 4(F+S) - (metric of state 0)
-        // every NORM_CHUNKS chunks, else 0; ES = 3: tn = 8F - (minimum over
-        // the states, taken at the end of the previous chunk) every chunk.
+        // before the stage would).  Min-normalised forms: tn = 2^ES F -
+        // (minimum over the states, taken at the end of the previous chunk)
+        // every chunk; the state-0 form: tn = 4(F+S) - (metric of state 0)
+        // every NORM_CHUNKS chunks, else 0.
         uint32_t tn = 0, tn1 = 0, tn2 = 0;
-        if constexpr (ES == 3) {
+        if constexpr (Cfg::MINNORM) {
             tn = sub_s16x2(SEED0, pmin);
             tn1 = add_u16x2(tn, 0x00010001u);   // -x + tn = ~x + tn1
             tn2 = add_u16x2(tn, 0x00020002u);   // -x + 1 + tn (odd candidates of stage 0)
@@ -870,7 +875,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     // and 16 + FW i (frame 1); fields cleared, half by a
                     // select (ALU) and half by a multiply-add (FMA pipe)
                     constexpr uint32_t FM = ((1u << ES) - 1u) * 0x00010001u;
-                    if constexpr (ES == 3 && S == U - 1) {
+                    if constexpr (Cfg::MINNORM && S == U - 1) {
                         // the minimum over the states for the next chunk's
                         // normalisation: min of 8 m + j, fields masked off
                         pmin = min_tree<NR>(P) & ~FM;
@@ -1083,9 +1088,15 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
 
     // ------------------------------------------------- traceback start state
     // After Wpad stages (a multiple of K-1) register R holds state R again.
+    // A frame that starts from the reset state and has fewer than K-1
+    // stages can only be in a state whose low K-1-W bits are zero (the
+    // others are -infinity for Algorithm 1 with a known start); the finite
+    // head start does not keep every such state below them, so they are
+    // left out of the argmax explicitly.
     uint32_t R[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+        const uint32_t unreach = (known[h] && W[h] < NB) ? ((1u << (NB - (int)W[h])) - 1u) : 0u;
         uint32_t best = 0;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -1093,6 +1104,16 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
             const uint32_t Rg = ((uint32_t)lane << LR) | (uint32_t)r;
             const uint32_t key = (v << 16) | (0xFFFFu - Rg);
             best = best > key ? best : key;
+        }
+        if (__builtin_expect(unreach != 0u, 0)) {
+            best = 0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t v = h ? (P[r] >> 16) : (P[r] & 0xFFFFu);
+                const uint32_t Rg = ((uint32_t)lane << LR) | (uint32_t)r;
+                const uint32_t key = (Rg & unreach) ? 0u : ((v << 16) | (0xFFFFu - Rg));
+                best = best > key ? best : key;
+            }
         }
         if constexpr (L > 1) {
 #pragma unroll

@@ -219,33 +219,38 @@ def _path_outputs(K, gens, s, inputs):
     return out
 
 
-@pytest.mark.parametrize("D", [51, 1, 32, 63])
-def test_head_start_adversarial_k7(D):
+@pytest.mark.parametrize("K,D", [(7, 51), (7, 1), (7, 32), (7, 63), (9, 191), (9, 1), (9, 229)])
+def test_head_start_adversarial(K, D):
     """The frame that starts from the reset state: its first K-1 stages carry
     saturated LLRs that match the path from start state D != 0 (zero inputs),
     so that path leads the path from state 0 with the same inputs by 254 per
-    differing output bit (2540 for D = 51 with the 171/133 code, the largest
-    lead any start state can take).  The oracle starts the other states at
+    differing output bit (2540 for D = 51 with the 171/133 code and 4826 for
+    D = 191 with 557/663/711, the largest lead any start state can take).
+    The oracle starts the other states at
     -infinity; the GPU's finite head start must keep the path from state 0
     ahead, which the frame's final canonical metrics show (the decoded bits
     cannot: both paths carry the same inputs).  The reset stage is swept over
     every position within a chunk of the kernel's unrolled stages."""
-    K, gens = 7, synth.K7_GENS
+    gens = synth.K7_GENS if K == 7 else synth.K9_GENS
+    beta, lanes = len(gens), (1 if K == 7 else 4)
     oc = oracle.Code(K, gens)
     code = gpu_code(K, gens)
     lead = np.array(_path_outputs(K, gens, D, [0] * (K - 1)))
-    for n, f, v in [(600 + i, 4096, 6) for i in range(6)] + [(700, 64, v) for v in range(6, 12)]:
+    U = 6 if K == 7 else 8   # stages per unrolled chunk of the kernel
+    cases = [(600 + i, 4096, 6) for i in range(U)] + [(700, 64, v) for v in range(6, 6 + U)]
+    for n, f, v in cases:
         rng = np.random.Generator(np.random.PCG64(4000 + 17 * D + n + v))
         q = synth.make_stream(rng, K, gens, n, 2.0, False).s8().copy()
-        q[:2 * (K - 1)] = np.where(lead == 0, 127, -127).astype(np.int8)
-        ow, opm = run_oracle(oc, q.reshape(n, 2).astype(np.int32), n, f, v)
-        gw, gpm = run_gpu(code, q, n, f, v, lanes=1)
+        q[:beta * (K - 1)] = np.where(lead == 0, 127, -127).astype(np.int8)
+        ow, opm = run_oracle(oc, q.reshape(n, beta).astype(np.int32), n, f, v)
+        gw, gpm = run_gpu(code, q, n, f, v, lanes=lanes)
         check(gw, gpm, ow, opm, K, n, f, v, n, False, False)
 
 
-@pytest.mark.parametrize("n,f,v,term", [(1, 32, 8, True), (70, 64, 3, False), (2000, 512, 64, True),
+@pytest.mark.parametrize("n,f,v,term", [(1, 32, 8, True), (5, 32, 8, False), (7, 64, 0, False),
+                                        (70, 64, 3, False), (2000, 512, 64, True),
                                         (2049, 1024, 700, False)])
-@pytest.mark.parametrize("kind", ["noisy", "zeros", "erasures"])
+@pytest.mark.parametrize("kind", ["noisy", "zeros", "saturated", "erasures"])
 def test_edge_cases_k9(n, f, v, term, kind):
     rng = np.random.Generator(np.random.PCG64(2000 + n + f + v))
     oc = oracle.Code(9, synth.K9_GENS)
@@ -254,6 +259,8 @@ def test_edge_cases_k9(n, f, v, term, kind):
         q = synth.make_stream(rng, 9, synth.K9_GENS, n, 1.0, term).s8()
     elif kind == "zeros":
         q = np.zeros(3 * T, np.int8)
+    elif kind == "saturated":
+        q = (127 * (1 - 2 * rng.integers(0, 2, 3 * T))).astype(np.int8)
     else:
         q = rng.integers(-127, 128, 3 * T).astype(np.int8)
         q[rng.random(3 * T) < 0.6] = 0
