@@ -305,7 +305,7 @@ struct TbState {
     int32_t tau_store;
     int32_t tauo[2], taue[2];
     int32_t toff[2];         // stage in the frame's stream = tau + toff
-    int32_t slot;            // staging slot holding group t0
+    int32_t slot;            // not read (a step walks both slots); keeps the record at 23 words
 
     __device__ __forceinline__ static uint64_t join(uint32_t lo, uint32_t hi) {
         return ((uint64_t)hi << 32) | lo;
