@@ -143,13 +143,17 @@ struct StreamCfg {
     static constexpr int TOPM = FM + (TOPM_STEADY > TOPM_RESET ? TOPM_STEADY : TOPM_RESET);
     static constexpr bool ES3_OK = !RADIX4 && NB % 3 == 0 && U % 3 == 0 && NR % 4 == 0 &&
                                    8 * TOPM + 7 <= 65535;
-    static constexpr bool ES2M_OK = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && 4 * TOPM + 3 <= 65535;
+    // Radix-4 takes stage-pair records: a field's two bits are the radix-4
+    // survivor of Eq. radix4:SP0 (the decision at the pair's second stage
+    // and that of the middle state it selects), the candidates grouped by
+    // middle state as two exact radix-2 steps (R10).
+    static constexpr bool ES2M_OK = NB % 2 == 0 && NR % 8 == 0 && 4 * TOPM + 3 <= 65535;
     // ES = 2 with state 0 as the reference every NORM_CHUNKS chunks and the
     // loose head start C::S (for codes whose min-normalised range does not
     // fit).  Longest normalisation period (stages) that keeps
     // 4 (F + 2S + (N+1) B) + 3 within 16 unsigned bits:
     static constexpr int NMAX_EMB = (16383 - 2 * C::S) / (2 * C::B) - 1;
-    static constexpr bool ES2_OK = !RADIX4 && NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
+    static constexpr bool ES2_OK = NB % 2 == 0 && NR % 8 == 0 && NMAX_EMB >= U;
     static constexpr int ES = ES3_OK ? 3 : ((ES2M_OK || ES2_OK) ? 2 : 0);
     static constexpr bool MINNORM = ES3_OK || ES2M_OK;
     static constexpr bool EMB = ES != 0;
@@ -365,7 +369,7 @@ struct Traceback {
     static constexpr int RW = EMB ? NR / RPW : NW;   // words per record and lane
     static constexpr int SLOT_WORDS = REC * 32 * RW;
     static constexpr int STAGE_WORDS = 2 * SLOT_WORDS;   // per warp
-    static_assert(!EMB || (G % ES == 0 && !RADIX4), "embedded decisions: radix-2, whole records per group");
+    static_assert(!EMB || (G % ES == 0 && (!RADIX4 || ES == 2)), "embedded decisions: whole records per group");
 
     // Copies the records of stages t0, t0-1, .., t0-G+1 (those >= tau_store)
     // to a slot (the caller commits the copies as one group).
