@@ -40,8 +40,11 @@
 //     middle state, as Eq. radix4:PM allows, gives exactly the same integers
 //     and ties), and the survivor of right state j is the 2-bit pair
 //     (d_m, d_i): the decision of j at stage t and the decision of the
-//     middle state it selects at stage t-1, stored at the same bit position
-//     so that one traceback step crosses two stages;
+//     middle state it selects at stage t-1 — exactly the 2-bit field of the
+//     embedded stage-pair records, which the radix-4 kernels use wherever
+//     their range fits (StreamCfg::ES2M_OK); otherwise the two bits go to
+//     per-stage decision words at the same bit position, so that one
+//     traceback step crosses two stages;
 //   * traceback (Algorithm 2) walks groups of K-1 stages whose survivor words
 //     are staged in shared memory; a group's decoded bits are the register
 //     index at the group's start.  The persistent kernels (vd_batch.cuh) run
