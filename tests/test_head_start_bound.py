@@ -58,3 +58,30 @@ def test_paths_that_meet_carry_the_same_inputs():
                 for w in itertools.product((0, 1), repeat=k):
                     if _walk(K, gens, D, u)[0] == _walk(K, gens, 0, w)[0]:
                         assert u == w
+
+
+def test_kernel_constants_match_the_brute_force(tmp_path):
+    """The decoder's compile-time DMAX and HT (Code<> in vd_device.cuh) equal
+    the brute-force bound above: a host-only program prints them (nvcc, no
+    GPU needed)."""
+    import os
+    import shutil
+    import subprocess
+    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc) and not shutil.which(nvcc):
+        pytest.skip("nvcc not found")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "ht.cu"
+    src.write_text(
+        '#include <cstdio>\n'
+        '#include "vd_device.cuh"\n'
+        'using C7 = vd::Code<7, 2, (uint64_t)0171 | ((uint64_t)0133 << 16)>;\n'
+        'using C9 = vd::Code<9, 3, (uint64_t)0557 | ((uint64_t)0663 << 16) | ((uint64_t)0711 << 32)>;\n'
+        'int main() { std::printf("%d %d %d %d\\n", C7::DMAX, C7::HT, C9::DMAX, C9::HT); return 0; }\n')
+    exe = tmp_path / "ht"
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(root, "paper_2011_13579_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    d7, ht7, d9, ht9 = map(int, subprocess.run([str(exe)], check=True, capture_output=True,
+                                                text=True).stdout.split())
+    assert (d7, d9) == (max_differing_bits(7, (0o171, 0o133)), max_differing_bits(9, (0o557, 0o663, 0o711)))
+    assert (ht7, ht9) == (254 * d7 + 1, 254 * d9 + 1)
