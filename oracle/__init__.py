@@ -12,7 +12,10 @@ it with ctypes over numpy arrays.
 Every function is pinned by ``tests/test_oracle_pins.py`` against facts that
 do not come from the oracle itself (noiseless channel, brute-force maximum
 likelihood, re-encoding, the paper's trellis theorems, textbook code facts).
-Parity unpinned: absolute BER values (the paper prints none).
+The per-frame canonical metric vector of ``decode(want_pm=True)`` and the
+``min_gap`` / ``max_abs_pm`` outputs of ``decode_f64`` are pinned by
+enumerating every path of small frames.  Parity unpinned: absolute BER
+values (the paper prints none).
 """
 from __future__ import annotations
 

@@ -516,3 +516,150 @@ def test_decode_frames_matches_full_decode():
         e = min(n, (s + 1) * f)
         assert np.array_equal(bits[k, : e - s * f], allbits[s * f: e])
         assert np.array_equal(pm_sel[k], pm[s])
+
+
+# ------------------------------------- metric vector and fp64 gaps, brute force
+
+def _enumerate_window(code, llr, starts):
+    """Every path through a window: for each start state in ``starts`` and
+    each input sequence of the window's W stages, the cumulative correlation
+    after l stages (l = 0..W) and the state after l stages.  Built from the
+    shift-register definition of Sec. II-A with this file's own encoder,
+    nothing from the oracle.  Returns (inputs [M, W], corr [M, W+1],
+    state [M, W+1])."""
+    K, beta = code.K, code.beta
+    W = llr.shape[0]
+    msgs = _all_messages(W)
+    hists, ins = [], []
+    for st in starts:
+        hist = np.array([(st >> k) & 1 for k in range(K - 1)], np.uint8)   # oldest first
+        hists.append(np.repeat(hist[None, :], msgs.shape[0], 0))
+        ins.append(msgs)
+    hist = np.concatenate(hists)
+    u = np.concatenate(ins)
+    seqs = np.concatenate([hist, u], axis=1)
+    cw = _batch_encode(K, code.gens, seqs)[:, K - 1:]                       # [M, W, beta]
+    per_stage = ((1 - 2 * cw.astype(np.float64)) * llr[None].astype(np.float64)).sum(axis=2)
+    corr = np.concatenate([np.zeros((seqs.shape[0], 1)), np.cumsum(per_stage, axis=1)], axis=1)
+    state = np.zeros((seqs.shape[0], W + 1), dtype=np.int64)
+    for l in range(W + 1):
+        # state after l stages: the last K-1 inputs, most recent as the MSB
+        for k in range(K - 1):
+            state[:, l] |= seqs[:, K - 2 + l - k].astype(np.int64) << (K - 2 - k)
+    return u, corr, state
+
+
+def _metric_vectors(code, corr, state):
+    """lambda_j after l stages = the best correlation of any path in state j
+    (Eq. PM unrolled: the maximum over whole paths), -inf if none reaches j."""
+    NS = code.n_states
+    L = np.full((corr.shape[1], NS), -np.inf)
+    for l in range(corr.shape[1]):
+        np.maximum.at(L[l], state[:, l], corr[:, l])
+    return L
+
+
+@pytest.mark.parametrize("K,gens", [(7, synth.K7_GENS), (5, (0o23, 0o35)), (4, (0o13, 0o15, 0o17))])
+@pytest.mark.parametrize("start_unknown", [False, True])
+@pytest.mark.parametrize("kind", ["random", "erasures"])
+def test_final_metric_vector_brute_force(K, gens, start_unknown, kind):
+    """The canonical final metric vector the oracle reports per frame
+    (lambda - min lambda after the frame's last stage, Eq. PM) equals the
+    best correlation of every path ending in each state, found by
+    enumerating all paths of the frame, minus its minimum.  Frames in the
+    middle of a stream start from any state (all-zero metrics, Algorithm 1);
+    the first frame from state 0 unless the start is unknown."""
+    code = oracle.Code(K, gens)
+    rng = np.random.Generator(np.random.PCG64(9001 + K + 7 * start_unknown + (kind == "erasures")))
+    n, f, v = 18, 6, 3                      # windows of up to f + 2v = 12 stages
+    T = oracle.n_stages(code, n, False)
+    for trial in range(3):
+        llr = rng.integers(-127, 128, size=(T, code.beta)).astype(np.int32)
+        if kind == "erasures":
+            llr[rng.random((T, code.beta)) < 0.6] = 0
+        _, pm = oracle.decode(code, llr, n, f=f, v=v, start_unknown=start_unknown, want_pm=True)
+        for s in range(-(-n // f)):
+            a, b = max(0, s * f - v), min(T, (s + 1) * f + v)
+            starts = [0] if (a == 0 and not start_unknown) else list(range(code.n_states))
+            _, corr, state = _enumerate_window(code, llr[a:b], starts)
+            lam = _metric_vectors(code, corr, state)[-1]
+            assert np.all(np.isfinite(lam))     # W >= K-1: every state is reachable
+            want = (lam - lam.min()).astype(np.int64)
+            assert np.array_equal(pm[s], want), (trial, s)
+
+
+def test_final_metric_vector_full_length_closed_form():
+    """Full length from state 0 on a noiseless codeword of amplitude 127:
+    the canonical vector equals the enumerated best correlation per end
+    state minus its minimum, the true end state holds the closed-form
+    maximum 127 * beta * T, and every other state is strictly below it."""
+    code = K7
+    rng = np.random.Generator(np.random.PCG64(4711))
+    n = 13
+    bits = synth.random_bits(rng, n)
+    llr = _noiseless_llr(code, bits, False)
+    _, pm = oracle.decode(code, llr, n, f=n, v=code.K, want_pm=True)
+    _, corr, state = _enumerate_window(code, llr, [0])
+    lam = _metric_vectors(code, corr, state)[-1]
+    assert np.array_equal(pm[0], (lam - lam.min()).astype(np.int64))
+    end = 0
+    for k in range(code.K - 1):
+        end |= int(bits[n - 1 - k]) << (code.K - 2 - k)
+    assert lam[end] == 127 * code.beta * n
+    assert np.all(np.delete(lam, end) < lam[end])
+
+
+@pytest.mark.parametrize("K,gens", [(7, synth.K7_GENS), (5, (0o23, 0o35))])
+@pytest.mark.parametrize("terminated,start_unknown", [(False, False), (True, False), (False, True)])
+def test_f64_gap_and_max_metric_brute_force(K, gens, terminated, start_unknown):
+    """The fp64 oracle's per-frame min_gap and max_abs_pm, pinned by
+    enumeration on continuous LLRs (no ties):
+      * the traced path is the best path into the traceback start state;
+      * at each traced stage t in [o, b) with state j after it, the decision
+        gap is |c1 - c0|, c_x = lambda_{p_x}(t) + delta(p_x -> j), where
+        lambda_{p_x}(t) + delta is the best correlation of the paths into j
+        whose previous state is p_x (Eq. PM / Eq. SP0);
+      * unless the frame ends at a terminated end, the best final metric
+        minus the runner-up is also a gap;
+      * max_abs_pm is the largest |lambda_j| of any reachable state after
+        any stage of the frame."""
+    code = oracle.Code(K, gens)
+    rng = np.random.Generator(np.random.PCG64(1234 + K + 2 * terminated + 5 * start_unknown))
+    n, f, v = 14, 5, 3
+    T = oracle.n_stages(code, n, terminated)
+    mask = code.n_states - 1
+    for trial in range(3):
+        llr = rng.normal(0.0, 2.0, size=(T, code.beta))
+        _, gap, mx = oracle.decode_f64(code, llr, n, f=f, v=v, terminated=terminated,
+                                       start_unknown=start_unknown)
+        for s in range(-(-n // f)):
+            o = s * f
+            a, b = max(0, o - v), min(T, (s + 1) * f + v)
+            starts = [0] if (a == 0 and not start_unknown) else list(range(code.n_states))
+            u, corr, state = _enumerate_window(code, llr[a:b], starts)
+            lam = _metric_vectors(code, corr, state)          # [W+1, NS]
+            W = b - a
+            want_mx = max(abs(x) for x in lam[1:].reshape(-1) if np.isfinite(x))
+            assert mx[s] == pytest.approx(want_mx, rel=1e-12, abs=1e-12), (trial, s)
+            gaps = []
+            if terminated and b == T:
+                js = 0
+            else:
+                fin = lam[W]
+                js = int(np.argmax(fin))
+                gaps.append(fin[js] - np.max(np.delete(fin, js)))
+            # the best path into js at the last stage, and its states
+            into = np.nonzero(state[:, W] == js)[0]
+            best = into[np.argmax(corr[into, W])]
+            path_states = state[best]
+            for t in range(b - 1, o - 1, -1):
+                l = t - a                      # stages done before stage t
+                j = int(path_states[l + 1])
+                p0 = (j << 1) & mask
+                c = []
+                for p in (p0, p0 | 1):
+                    sel = np.nonzero((state[:, l] == p) & (state[:, l + 1] == j))[0]
+                    c.append(np.max(corr[sel, l + 1]) if sel.size else -np.inf)
+                gaps.append(abs(c[1] - c[0]))
+            want_gap = min(gaps)
+            assert gap[s] == pytest.approx(want_gap, rel=1e-9, abs=1e-9), (trial, s)
