@@ -36,12 +36,13 @@ PLAIN_STREAMS = 32
 
 
 def workload_config(radix, lanes, path="batch"):
+    paths = {"batch": "one persistent batched launch per step (vd_batch_plan_launch)",
+             "stream": "one vd_decode launch per stream",
+             "oracle": "CPU oracle (int64 radix-2), bounded sample of one stream per step"}
     return {"workload": "segmented stream decode, K=7 r1/2 (171,133), 6 streams x 2^24 info bits, "
                         "Eb/N0 1..6 dB, f=256, v=42, int8 LLR",
             "n_info_per_stream": N_INFO, "streams_per_step": len(EBN0S), "f": F, "v": V,
-            "radix": radix, "lanes": lanes,
-            "path": ("one persistent batched launch per step (vd_batch_plan_launch)" if path == "batch"
-                     else "one vd_decode launch per stream"),
+            "radix": radix, "lanes": lanes, "path": paths[path],
             "l2": "inputs larger than L2 (192 MiB cycled per step)"}
 
 
@@ -339,12 +340,25 @@ def run_gpu(args, rank, world):
     ref_bits = synth.segmented_stream(6.0).bits
     ber6 = float(np.mean(bits != ref_bits))
 
+    # decoded words of every stream, radix 2 (the timed plan's last run) and
+    # radix 4 (one launch of a radix-4 plan), for the segmentation-BER leg
+    words_r2 = words_r4 = None
+    if plan is not None and rank == 0 and world == 1 and not args.no_ber:
+        words_r2 = [o.cpu().numpy().view(np.uint32).copy() for o in outs]
+        p4 = stream_plan(vd, code, len(streams), 4, 0, s)
+        p4.launch(arena, out_arena, stream=s)
+        torch.cuda.synchronize(dev)
+        p4.status(stream=s)
+        words_r4 = [o.cpu().numpy().view(np.uint32).copy() for o in outs]
+        p4.close()
+
     if plan is not None:
         plan.close()
     packets = None
     if rank == 0 and args.packets > 0:
         packets = run_packets(args, dev, s)
     return {"shape": shape, "packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
+            "words_r2": words_r2, "words_r4": words_r4,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
@@ -539,6 +553,99 @@ def run_bm_gate(dev, s):
     return res
 
 
+INT_PEAK_VARIANTS = (
+    # (variant, name, instructions per body, algorithmic ops per body or None)
+    (0, "add.u16x2", 8, None), (1, "max.u16x2", 8, None), (2, "add+max.u16x2 (fused)", 8, None),
+    (3, "mad.lo.u32", 8, None), (4, "lop3.b32", 8, None), (5, "prmt.b32", 8, None),
+    (6, "shf.l.wrap.b32", 8, None), (7, "add.u16x2 + mad.lo.u32 (1:1)", 8, None),
+    (8, "add+max.u16x2 + mad.lo.u32 (1:1)", 8, None), (9, "max.u16x2 + lop3.b32 (1:1)", 8, None),
+    (10, "radix-2 butterfly: 2 add.u16x2 + 2 add+max.u16x2", 16, 48),
+)
+
+
+# The SM pipe each single-class variant issues to, read once from ncu's
+# sm__inst_executed_pipe_{alu,fmaheavy} counters on GB300 (profiles/int_peak_gb300.md):
+# 16x2 add and 32-bit multiply-add on the FMA pipe; fused add-max, 16x2 max,
+# three-input logic, byte permute and funnel shift on the ALU pipe.
+INT_PEAK_PIPE = {0: "fma", 1: "alu", 2: "alu", 3: "fma", 4: "alu", 5: "alu", 6: "alu"}
+
+
+def run_int_peak(dev, s, iters=2048):
+    """Integer-issue rates on this GPU (vd_int_peak): per variant, thread-level
+    operations per SM per SM-clock, from each block's clock64() span (one block
+    of 1024 threads per SM, 8 chains per thread).  The roofline's peak lane
+    rate is the ALU pipe's best single-class rate plus the FMA pipe's (the two
+    pipes issue concurrently; the decoder's instructions all run on them); the
+    butterfly variant is the ACS alone (12 algorithmic ops per 4
+    instructions), and the 1:1 mixes show how close two classes get to the sum."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    cyc = torch.zeros(n_sm, dtype=torch.int64, device=dev)
+    sink = torch.zeros(n_sm * 1024, dtype=torch.int32, device=dev)
+    res = []
+    for var, name, ipb, apb in INT_PEAK_VARIANTS:
+        vd.vd_int_peak(var, 64, n_sm, cyc, sink, stream=s)      # warm-up
+        vd.vd_int_peak(var, iters, n_sm, cyc, sink, stream=s)
+        torch.cuda.synchronize(dev)
+        c = cyc.cpu().numpy().astype(np.float64)
+        ops = 1024.0 * iters * 16 * ipb                           # thread instructions per SM
+        r = {"variant": var, "ops": name, "per_sm_per_clk": float(ops / np.median(c)),
+             "cycles_median": float(np.median(c)), "cycles_max": float(np.max(c))}
+        if apb:
+            r["alg_ops_per_sm_per_clk"] = float(1024.0 * iters * 16 * apb / np.median(c))
+        res.append(r)
+    alu = max(r["per_sm_per_clk"] for r in res if INT_PEAK_PIPE.get(r["variant"]) == "alu")
+    fma = max(r["per_sm_per_clk"] for r in res if INT_PEAK_PIPE.get(r["variant"]) == "fma")
+    mix = max(r["per_sm_per_clk"] for r in res if r["variant"] in (7, 8, 9))
+    return {"n_sm": n_sm, "iters": iters, "variants": res, "lanes_per_sm_per_clk": alu + fma,
+            "alu_lanes_per_sm_per_clk": alu, "fma_lanes_per_sm_per_clk": fma,
+            "best_two_class_mix_per_sm_per_clk": mix,
+            "lanes_from": f"ALU pipe {alu:.1f} + FMA pipe {fma:.1f}",
+            "butterfly_alg_ops_per_sm_per_clk": next(r["alg_ops_per_sm_per_clk"] for r in res
+                                                     if r["variant"] == 10)}
+
+
+def run_ber(args, outs_r2, outs_r4):
+    """BER cost of segmentation on the bench's six 2^24-bit streams (Sec. III:
+    frames trade BER for parallelism): per Eb/N0, the GPU's segmented decode
+    (radix 2 and radix 4, which must agree bit for bit) against the true bits,
+    the segmented oracle (bit-exactness) and the full-length oracle decode
+    (one frame over the whole stream, one host thread per stream).  BER at or
+    below 100/n is reported as "< floor"."""
+    import concurrent.futures as cf
+    import oracle
+    from paper_2011_13579_gb300 import synth
+    oracle.build()
+    code = oracle.Code(K, synth.K7_GENS)
+    threads = len(os.sched_getaffinity(0))
+    floor = 100.0 / N_INFO
+    streams = [synth.segmented_stream(e) for e in EBN0S]
+    qs = [st.s8().reshape(-1, BETA).astype(np.int32) for st in streams]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=min(len(streams), threads)) as ex:
+        fulls = list(ex.map(lambda q: oracle.unpack_bits(oracle.decode_full(code, q, N_INFO), N_INFO), qs))
+    t_full = time.perf_counter() - t0
+
+    def fmt(x):
+        return x if x > floor else f"< {floor:.2e}"
+
+    pts = []
+    for e, st, q, full, g2, g4 in zip(EBN0S, streams, qs, fulls, outs_r2, outs_r4):
+        seg = oracle.unpack_bits(oracle.decode(code, q, N_INFO, F, V, threads=threads), N_INFO)
+        b2 = oracle.unpack_bits(g2, N_INFO)
+        b4 = oracle.unpack_bits(g4, N_INFO)
+        ber_full = float(np.mean(full != st.bits))
+        ber_seg = float(np.mean(b2 != st.bits))
+        pts.append({"ebn0_db": e, "ber_full_length_oracle": fmt(ber_full), "ber_segmented_gpu": fmt(ber_seg),
+                    "ber_cost": ber_seg - ber_full,
+                    "bits_differing_segmented_vs_full": int(np.count_nonzero(b2 != full)),
+                    "gpu_radix2_equals_segmented_oracle": bool(np.array_equal(b2, seg)),
+                    "gpu_radix4_equals_radix2": bool(np.array_equal(b4, b2))})
+    return {"workload": "6 streams x 2^24 info bits, K=7 r1/2, f=256, v=42, int8 LLR, unterminated",
+            "ber_floor": floor, "full_length_oracle_s": t_full, "points": pts}
+
+
 def run_precision(args):
     """Precision study on the (3,1,9) 557/663/711 code: 2^24 information bits
     per Eb/N0 in 0..4 dB, f=512, v=64, decoded on the GPU three ways — int8 and
@@ -695,13 +802,16 @@ def main():
     ap.add_argument("--no-bm-gate", action="store_true", help="skip the branch-metric CUDA/tensor-core gate")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-loads", type=lambda t: [float(x) for x in t.split(",")] if t else [],
-                    default=[0.1, 0.5, 0.9], help="offered loads (fractions of peak); empty: skip serving")
+                    default=[round(0.1 * i, 1) for i in range(1, 11)],
+                    help="offered loads (fractions of peak); empty: skip serving")
     ap.add_argument("--serving-pool", type=int, default=8192)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-max-packets", type=int, default=400000)
-    ap.add_argument("--workload", default="stream", choices=["stream", "precision", "packets"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "precision", "packets", "intpeak"],
                     help="precision: the K=9 precision study (int8 / 4-bit / fp16) instead of the bench line; "
-                         "packets: only W+K graph launches of the uneven-packet plan (for profilers)")
+                         "packets: only W+K graph launches of the uneven-packet plan (for profilers); "
+                         "intpeak: only the integer-issue microbenchmark")
+    ap.add_argument("--no-ber", action="store_true", help="skip the segmentation-BER leg (CPU oracle)")
     ap.add_argument("--precision-bits", type=int, default=1 << 24)
     ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.0, 1.0, 2.0, 3.0, 4.0])
@@ -736,7 +846,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": workload_config(2, 1),
+                "config": workload_config(2, 1, path="oracle"),
                 "cpu_baseline": {**vals[-1], "value": v},
                 "e2e": {"value": v, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -754,6 +864,11 @@ def main():
     if args.workload == "packets":
         packets_only(args)
         return
+    if args.workload == "intpeak":
+        import torch
+        print(json.dumps({"int_peak": run_int_peak(torch.device("cuda", 0), torch.cuda.current_stream())}),
+              flush=True)
+        return
     if args.mode == "kernel":
         kernel_only(args)
         return
@@ -765,12 +880,19 @@ def main():
             dist.destroy_process_group()
         return
 
+    import torch
     peaks = load_peaks()
     n_sm = r["n_sm"]
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    # ALU roofline: 128 integer lanes per SM per clock, each 16x2 instruction
-    # carrying two frames (two 16-bit halves), at the maximum SM clock
-    peak_ops = n_sm * 128 * 2 * sm_max_mhz * 1e6
+    # Integer roofline: the integer lanes per SM per clock measured by the
+    # vd_int_peak microbenchmark on this GPU (best instruction class or 1:1
+    # mix), each 16x2 instruction carrying two frames (two 16-bit halves), at
+    # the maximum SM clock.  The fused add-then-max of the butterfly does two
+    # algorithmic operations per half in one lane slot, so frac = 1 is not a
+    # ceiling: the ACS alone (the butterfly variant) reaches more.
+    ip = run_int_peak(torch.device("cuda", 0), torch.cuda.current_stream())
+    lanes = ip["lanes_per_sm_per_clk"]
+    peak_ops = n_sm * lanes * 2 * sm_max_mhz * 1e6
     launch_ms = r["launch_ms"]
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     ops_per_launch = ops_per_bit() * r["bits_per_launch"]
@@ -797,7 +919,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u16x2",
+        "dtype": "int8 LLR / exact 16x2 metrics",
         "data": "synthetic",
         "config": {**workload_config(r["shape"]["radix"], r["shape"]["lanes"], args.path),
                    "parallelism": f"replicas{world}"},
@@ -806,7 +928,13 @@ def main():
                      "kernel": "vd::batch_kernel" if args.path == "batch" else "vd::stream_kernel",
                      "avg_launch_ms": avg_launch_s * 1e3,
                      "ops_per_bit": ops_per_bit(),
-                     "peak_basis": f"{n_sm} SMs x 128 lanes x 2 halves x {sm_max_mhz:.0f} MHz"},
+                     "peak_basis": (f"{n_sm} SMs x {lanes:.1f} integer lanes per SM per clock (measured by "
+                                    f"vd_int_peak: {ip['lanes_from']}) x 2 halves (16x2) x {sm_max_mhz:.0f} MHz "
+                                    "max SM clock; a fused add-then-max counts 2 algorithmic ops per half in one "
+                                    "lane slot, so frac = 1 is not the ceiling: the ACS alone reaches "
+                                    f"{ip['butterfly_alg_ops_per_sm_per_clk'] / (2 * lanes):.2f} of this peak"),
+                     "issue_ceiling_acs_only": ip["butterfly_alg_ops_per_sm_per_clk"] / (2 * lanes)},
+        "int_peak": ip,
         "e2e": r["e2e"],
         "gpu_launches": args.steps * r["launches_per_step"],
         "clocks": r["clocks"],
@@ -814,6 +942,8 @@ def main():
     }
     if r.get("packets"):
         line["batched_vs_plain"] = r["packets"]
+    if world == 1 and r.get("words_r2") is not None:
+        line["segmentation_ber"] = run_ber(args, r["words_r2"], r["words_r4"])
     if world == 1 and args.serving_loads:
         line["serving"] = run_serving(args)
         line["serving_device"] = run_serving(args, device_resident=True)

@@ -67,7 +67,13 @@ typedef enum {
 /* LLR element types */
 enum { VD_LLR_S8 = 0,      /* int8 in [-127, 127] */
        VD_LLR_S4 = 1,      /* 4-bit in [-7, 7], two per byte, low nibble = earlier value */
-       VD_LLR_F16 = 2 };   /* IEEE half; metrics in fp32 */
+       VD_LLR_F16 = 2,     /* IEEE half; metrics in fp32 */
+       VD_LLR_HARD = 3 };  /* hard decisions (Sec. II-C, hard-decision mode): one bit per
+                              received value, the detected code bit, eight per byte with the
+                              earliest value in bit 0.  Decoded as LLR +1 (bit 0) or -1 (bit 1):
+                              Eq. BM then gives beta - 2 x (Hamming distance between the branch
+                              output and the received bits) on unpunctured stages, so the
+                              maximum-metric path is the minimum-Hamming-distance path. */
 
 /* flags */
 enum { VD_TERMINATED = 1u,     /* stream ends with k-1 zero tail inputs (state 0) */
@@ -352,9 +358,30 @@ vd_status vd_bm_gate(int variant, const void *d_llr, int64_t n_pairs, int32_t n_
                      uint32_t *d_checksum, uint32_t *d_metrics, void *stream);
 
 /*
- * Waits for the stream, then reads and clears the library's device status
- * word.  VD_EBOUNDS if a kernel refused work that would have overrun its
- * scratch since the last check (the affected outputs are not written).
+ * vd_int_peak — the integer-issue microbenchmark behind the decoder's
+ * roofline (the add-compare-select of Eq. PM runs on the SM's integer units).
+ * Runs one variant on n_blocks blocks of 1024 threads (one per SM), each
+ * thread 8 independent dependency chains for iters x 16 bodies:
+ *   0: 16x2 add   1: 16x2 max   2: fused 16x2 add-then-max   3: 32-bit
+ *   multiply-add   4: three-input logic   5: byte permute   6: funnel shift
+ *   7: 16x2 add + multiply-add, 1:1   8: fused add-max + multiply-add, 1:1
+ *   9: 16x2 max + three-input logic, 1:1   10: the decoder's radix-2
+ *   butterfly (two 16x2 adds and two fused add-max per register pair).
+ * A body is 8 operations of the variant (16 for variant 10: 4 butterflies).
+ *   d_cycles: [n_blocks] int64 — each block's clock64() span between two block
+ *             barriers around the timed loop (SM clocks).
+ *   d_sink:   [n_blocks x 1024] words the chains are folded into.
+ * Asynchronous on stream; VD_EINVAL on bad arguments, VD_ECUDA on launch failure.
+ */
+vd_status vd_int_peak(int variant, int64_t iters, int n_blocks, int64_t *d_cycles, uint32_t *d_sink,
+                      void *stream);
+
+/*
+ * Waits for the stream, then reads and clears the device status words of the
+ * current device: that of vd_decode_noalloc first, then the library's own.
+ * VD_EBOUNDS if a kernel refused work that would have overrun its scratch
+ * since the last check (the affected outputs are not written).  Allocates
+ * nothing (a status word that does not exist yet has not been written).
  */
 vd_status vd_sync(void *stream);
 
@@ -377,13 +404,21 @@ vd_status vd_sync(void *stream);
  * sizes (for the K=7 code at f=256, v=42 this is about 2 million info bits).
  *
  * Arguments as vd_decode, restricted to unpunctured int8 LLRs (VD_LLR_S8);
- * no metric output.  The first call on each device looks up the device
- * address of the array (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call on a device shares
- * the one array: calls that overlap on the GPU (different streams, or
- * concurrent host threads) race on it and corrupt each other's results;
- * serialise them (one stream).  A status word in a second static array is
- * cleared by every call.
+ * no metric output.  The first call on each device sets that device up: it
+ * looks up the device address of the array (cudaGetSymbolAddress) with the
+ * device current, which under lazy module loading also loads the library's
+ * device code and materialises the array.  So make one call first, before
+ * the phase that must not allocate and before any stream capture; a call
+ * with n_info = 0 does only this set-up.  Every call on a device shares the
+ * one array: calls that overlap on the GPU (different streams, or concurrent
+ * host threads) race on it and corrupt each other's results; serialise them
+ * (one stream).
+ *
+ * Device-side errors: a kernel that refuses a frame pair which would overrun
+ * the array (host checks make this unreachable) sets a status word in a
+ * second static array and leaves that pair's output unwritten.  The word is
+ * zero at load, is not cleared by decode calls, and is read and cleared by
+ * vd_sync(stream), which then returns VD_EBOUNDS.
  */
 vd_status vd_decode_noalloc(const vd_code *code, const void *d_llr, int64_t n_info, int f, int v,
                             int radix, uint32_t flags, uint32_t *d_out, void *stream);

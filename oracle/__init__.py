@@ -92,6 +92,8 @@ def _load():
         lib.or_decode_frames_i64.argtypes = [P(_Code), P(i32), i64, ctypes.c_int, ctypes.c_int,
                                              i64, i64, P(i64), i64, P(u8), P(i64)]
         lib.or_decode_frames_i64.restype = ctypes.c_int
+        lib.or_decode_hard.argtypes = [P(_Code), P(u8), i64, ctypes.c_int, ctypes.c_int, i64, i64, P(u32)]
+        lib.or_decode_hard.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -218,6 +220,31 @@ def decode_f64(code: Code, llr, n_info: int, f: int, v: int, terminated=False,
     if rc != 0:
         raise RuntimeError(f"oracle decode_f64 failed ({rc})")
     return out[: (n_info + 31) // 32], gap[:nwin], mx[:nwin]
+
+
+def depuncture_hard(code: Code, kept_bits, T: int):
+    """Kept-only hard decisions (0/1) -> [T, beta] uint8 with 2 at erased positions."""
+    kept = np.ascontiguousarray(kept_bits, dtype=np.int32).reshape(-1)
+    full = depuncture(code, kept + 1, T)          # erased positions come back as 0
+    return np.where(full == 0, 2, full - 1).astype(np.uint8)
+
+
+def decode_hard(code: Code, rx, n_info: int, f: int, v: int, terminated=False, start_unknown=False):
+    """Hard-decision decode (minimum Hamming distance, Sec. II-C).  ``rx`` is
+    [T, beta] uint8: 0/1 received bits, 2 at erased positions.  Returns
+    packed LSB-first uint32 words."""
+    lib = _load()
+    T = n_stages(code, n_info, terminated)
+    rx = np.ascontiguousarray(rx, dtype=np.uint8).reshape(-1)
+    if rx.size != T * code.beta:
+        raise ValueError("rx size mismatch")
+    out = np.zeros(max(1, (n_info + 31) // 32), dtype=np.uint32)
+    rc = lib.or_decode_hard(ctypes.byref(code._c), _ptr(rx, ctypes.c_uint8), n_info,
+                            int(bool(terminated)), int(bool(start_unknown)), f, v,
+                            _ptr(out, ctypes.c_uint32))
+    if rc != 0:
+        raise RuntimeError(f"oracle decode_hard failed ({rc})")
+    return out[: (n_info + 31) // 32]
 
 
 def decode_frames(code: Code, llr, n_info: int, f: int, v: int, frames, terminated=False,

@@ -549,3 +549,74 @@ done:
     free(bits); free(pm); free(pm_new); free(fpm); free(phi);
     return rc;
 }
+
+/* --------------------------------------------- hard decisions, Sec. II-C */
+
+/*
+ * Hard-decision decode (Sec. II-C, hard-decision mode: every received value
+ * is a bit).  rx is [T][beta] with 0 or 1 per received bit and 2 at a
+ * position the puncturing pattern erased (it carries no information).  The
+ * branch metric is the Hamming distance between the branch output and the
+ * received bits over the positions that are not erased; the path metric of
+ * a state is the smallest accumulated distance of a path into it (the
+ * forward procedure of Algorithm 1 with the distance minimised), and a tie
+ * keeps the second predecessor, as the strict comparison of Algorithm 1
+ * does; the traceback (Algorithm 2) starts from the state with the smallest
+ * distance, the lowest index on ties, or from state 0 at a terminated end.
+ * Frames as in or_decode_i64; a frame at stage 0 starts from state 0 (the
+ * others at an infinite distance) unless the start is unknown.
+ */
+int or_decode_hard(const or_code *c, const uint8_t *rx, int64_t n_info, int terminated,
+                   int start_unknown, int64_t f, int64_t v, uint32_t *out)
+{
+    if (or_check_code(c) || n_info < 0 || f <= 0 || v < 0) return -1;
+    if (n_info == 0) return 0;
+    const int NS = 1 << (c->K - 1);
+    const uint32_t mask = (uint32_t)NS - 1u;
+    const int64_t T = n_info + (terminated ? c->K - 1 : 0);
+    const int64_t INF = INT64_MAX / 4;
+    int64_t Wmax = f + 2 * v;
+    if (Wmax > T) Wmax = T;
+    uint8_t *bits = (uint8_t *)calloc((size_t)n_info, 1);
+    int64_t *d = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS);
+    int64_t *dn = (int64_t *)malloc(sizeof(int64_t) * (size_t)NS);
+    uint8_t *phi = (uint8_t *)malloc((size_t)(Wmax > 0 ? Wmax : 1) * (size_t)NS);
+    if (!bits || !d || !dn || !phi) { free(bits); free(d); free(dn); free(phi); return -2; }
+    const int64_t nwin = or_num_windows(n_info, f);
+    for (int64_t s = 0; s < nwin; ++s) {
+        or_window w = or_window_of(s, n_info, T, f, v);
+        for (int j = 0; j < NS; ++j) d[j] = 0;
+        if (w.a == 0 && !start_unknown)
+            for (int j = 1; j < NS; ++j) d[j] = INF;
+        for (int64_t t = w.a; t < w.b; ++t) {
+            const uint8_t *r = rx + t * c->beta;
+            uint8_t *ph = phi + (t - w.a) * NS;
+            for (uint32_t j = 0; j < (uint32_t)NS; ++j) {
+                const int u = (int)(j >> (c->K - 2));
+                const uint32_t p0 = (j << 1) & mask, p1 = p0 | 1u;
+                int64_t h0 = 0, h1 = 0;
+                for (int b = 0; b < c->beta; ++b) {
+                    if (r[b] > 1) continue;                       /* erased */
+                    h0 += or_out_bit(c, p0, u, b) != r[b];
+                    h1 += or_out_bit(c, p1, u, b) != r[b];
+                }
+                const int64_t c0 = d[p0] + h0, c1 = d[p1] + h1;
+                if (c0 < c1) { dn[j] = c0; ph[j] = 0; }
+                else         { dn[j] = c1; ph[j] = 1; }
+            }
+            memcpy(d, dn, sizeof(int64_t) * (size_t)NS);
+        }
+        uint32_t js = 0;
+        if (!(w.b == T && terminated)) {
+            for (uint32_t j = 1; j < (uint32_t)NS; ++j)
+                if (d[j] < d[js]) js = j;
+        }
+        for (int64_t t = w.b - 1; t >= w.o; --t) {
+            if (t < w.e) bits[t] = (uint8_t)(js >> (c->K - 2));
+            js = ((js << 1) & mask) | phi[(t - w.a) * NS + js];
+        }
+    }
+    or_pack_bits(bits, n_info, out);
+    free(bits); free(d); free(dn); free(phi);
+    return 0;
+}

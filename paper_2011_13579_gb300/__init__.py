@@ -19,18 +19,18 @@ from . import _build
 
 __all__ = [
     "VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_EUNSUPPORTED", "VD_ETIMEOUT", "VD_EBOUNDS",
-    "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_TERMINATED", "VD_START_UNKNOWN",
+    "VD_LLR_S8", "VD_LLR_S4", "VD_LLR_F16", "VD_LLR_HARD", "VD_TERMINATED", "VD_START_UNKNOWN",
     "VdError", "VdTune", "build", "lib", "vd_code_create", "vd_code_destroy", "vd_code_supported",
     "vd_decode", "vd_decode_batch", "vd_batch_plan_create", "vd_batch_plan_launch",
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_int_peak", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
 VD_OK, VD_EINVAL, VD_ENOMEM, VD_ECUDA, VD_EUNSUPPORTED, VD_ETIMEOUT, VD_EBOUNDS = 0, -1, -2, -3, -4, -5, -6
-VD_LLR_S8, VD_LLR_S4, VD_LLR_F16 = 0, 1, 2
+VD_LLR_S8, VD_LLR_S4, VD_LLR_F16, VD_LLR_HARD = 0, 1, 2, 3
 VD_TERMINATED, VD_START_UNKNOWN = 1, 2
 
 _STATUS = {0: "VD_OK", -1: "VD_EINVAL", -2: "VD_ENOMEM", -3: "VD_ECUDA", -4: "VD_EUNSUPPORTED",
@@ -159,6 +159,8 @@ def lib():
         L.vd_get_tune.restype = i32
         L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
         L.vd_bm_gate.restype = i32
+        L.vd_int_peak.argtypes = [i32, i64, i32, vp, vp, vp]
+        L.vd_int_peak.restype = i32
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -242,6 +244,14 @@ def vd_bm_gate(variant, llr_words, n_pairs, n_stages, checksum, metrics=None, st
                             ctypes.c_void_p(checksum.data_ptr()),
                             ctypes.c_void_p(metrics.data_ptr()) if metrics is not None else None,
                             _stream_handle(stream)))
+
+
+def vd_int_peak(variant, iters, n_blocks, cycles, sink, stream=None) -> None:
+    """Integer-issue microbenchmark on device tensors: cycles (int64
+    [n_blocks]) receives each block's SM-clock span, sink (int32
+    [n_blocks * 1024]) the folded chains."""
+    _check(lib().vd_int_peak(int(variant), int(iters), int(n_blocks), ctypes.c_void_p(cycles.data_ptr()),
+                             ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream)))
 
 
 def vd_get_tune(handle, llr_type, f, v, radix) -> "VdTune":

@@ -201,15 +201,27 @@ vd_status device_status_word(cudaStream_t st, int **out) {
     return VD_OK;
 }
 
+// The library's status word of the current device, or NULL if no call has
+// created it yet (then no kernel can have written it).
+int *existing_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    auto it = g_scratch.find(std::make_tuple(dev, (uintptr_t)0, 2));
+    return it == g_scratch.end() ? nullptr : (int *)it->second.ptr;
+}
+
 }  // namespace
 
 extern "C" vd_status vd_sync(void *stream) {
     cudaStream_t cs = (cudaStream_t)stream;
     cudaError_t e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    int *status = nullptr;
-    vd_status st = device_status_word(cs, &status);
-    if (st != VD_OK) return st;
+    // the no-allocation entry point's own status word first (it allocates nothing)
+    const vd_status na = vd_internal_noalloc_status();
+    if (na != VD_OK) return na;
+    int *status = existing_status_word();
+    if (!status) return VD_OK;
     int h = 0;
     e = cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
@@ -377,7 +389,7 @@ vd_status check_decode_args(const vd_code *c, const void *d_llr, int llr_type, i
     if (radix != 2 && radix != 4) return fail(VD_EINVAL, "radix must be 2 or 4");
     if (flags & ~(uint32_t)(VD_TERMINATED | VD_START_UNKNOWN))
         return fail(VD_EINVAL, "unknown flag bits 0x%x", flags);
-    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16)
+    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16 && llr_type != VD_LLR_HARD)
         return fail(VD_EINVAL, "unknown llr_type %d", llr_type);
     if (n_info > 0 && (!d_llr || !d_out)) return fail(VD_EINVAL, "NULL device pointer");
     if (n_info > 0 && f < n_info && f % 32 != 0)
@@ -413,7 +425,7 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     if (st != VD_OK) return st;
 
     const int8_t *llr = (const int8_t *)d_llr;
-    if (!f32 && (c->punctured || llr_type == VD_LLR_S4)) {
+    if (!f32 && (c->punctured || llr_type == VD_LLR_S4 || llr_type == VD_LLR_HARD)) {
         void *buf = nullptr;
         st = get_scratch(1, (size_t)pl.T * c->beta, cs, &buf);
         if (st != VD_OK) return st;
@@ -495,7 +507,7 @@ extern "C" vd_status vd_get_tune(const vd_code *c, int llr_type, int f, int v, i
     if (!c || !out) return fail(VD_EINVAL, "NULL argument");
     if (f <= 0 || v < 0) return fail(VD_EINVAL, "f must be positive and v >= 0");
     if (radix != 2 && radix != 4) return fail(VD_EINVAL, "radix must be 2 or 4");
-    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16)
+    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_F16 && llr_type != VD_LLR_HARD)
         return fail(VD_EINVAL, "unknown llr_type %d", llr_type);
     memset(out, 0, sizeof *out);
     const bool f32 = llr_type == VD_LLR_F16;

@@ -307,8 +307,9 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
     for (int64_t i = 0; i < n_packets; ++i) {
         const vd_packet &p = packets[i];
         if (p.code_id < 0 || p.code_id >= n_codes) return fail(VD_EINVAL, "packet %lld: bad code_id", (long long)i);
-        if (p.llr_type != VD_LLR_S8 && p.llr_type != VD_LLR_S4)
-            return fail(VD_EUNSUPPORTED, "packet %lld: batches take int8 or 4-bit LLRs", (long long)i);
+        if (p.llr_type != VD_LLR_S8 && p.llr_type != VD_LLR_S4 && p.llr_type != VD_LLR_HARD)
+            return fail(VD_EUNSUPPORTED, "packet %lld: batches take int8, 4-bit or hard-decision input",
+                        (long long)i);
         if (p.n_info <= 0) return fail(VD_EINVAL, "packet %lld: n_info must be positive", (long long)i);
         if (p.f < 0 || p.v < 0) return fail(VD_EINVAL, "packet %lld: negative f or v", (long long)i);
         if (p.f > 0 && p.f < p.n_info && p.f % 32)
@@ -317,6 +318,8 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
             return fail(VD_EINVAL, "packet %lld: negative offset", (long long)i);
         if (p.llr_type == VD_LLR_S4 && (p.llr_offset & 1))
             return fail(VD_EINVAL, "packet %lld: 4-bit packets must start on a byte", (long long)i);
+        if (p.llr_type == VD_LLR_HARD && (p.llr_offset & 7))
+            return fail(VD_EINVAL, "packet %lld: hard-decision packets must start on a byte", (long long)i);
         if (p.flags & ~(uint32_t)(VD_TERMINATED | VD_START_UNKNOWN))
             return fail(VD_EINVAL, "packet %lld: unknown flags", (long long)i);
     }
@@ -346,7 +349,7 @@ extern "C" vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *co
     for (int64_t i = 0; i < n_packets; ++i) {
         const vd_packet &p = packets[i];
         const vd_code *c = codes[p.code_id];
-        if (c->punctured || p.llr_type == VD_LLR_S4) {
+        if (c->punctured || p.llr_type == VD_LLR_S4 || p.llr_type == VD_LLR_HARD) {
             const int64_t T = p.n_info + ((p.flags & VD_TERMINATED) ? c->K - 1 : 0);
             PrepJob j;
             j.src = nullptr;

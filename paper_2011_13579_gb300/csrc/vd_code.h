@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/vd.h"
 #include "vd_launch.h"
 
 struct vd_code {
@@ -18,6 +19,10 @@ struct vd_code {
 
 // Sets the calling thread's message returned by vd_last_error().
 void vd_internal_set_error(const char *msg);
+
+// Reads and clears the device status word of vd_decode_noalloc on the current
+// device (VD_EBOUNDS if a kernel set it); called by vd_sync.
+vd_status vd_internal_noalloc_status(void);
 
 namespace vd {
 

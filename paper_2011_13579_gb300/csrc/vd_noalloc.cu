@@ -33,8 +33,11 @@ constexpr int kMaxDevices = 64;
 // calls and nothing in it needs to start at zero (every word the traceback
 // reads is written earlier in the same launch).
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocScratchBytes / 4];
-// Device status word of these launches (must start at zero: cleared per call).
-static __device__ __align__(256) int g_noalloc_status[64];
+// Device status word of these launches: a kernel ORs bit 0 into it if it
+// refuses a frame pair that would overrun the scratch.  Zero at load; read
+// and cleared by vd_sync (vd_internal_noalloc_status), never by a decode
+// call, so an error is reported even when several calls ran before it.
+static __device__ __align__(256) int g_noalloc_status[1];
 
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices];
@@ -77,6 +80,32 @@ vd_status device_arrays(void **scratch, int **status) {
 
 }  // namespace
 
+// Reads and clears this device's noalloc status word, if a noalloc call has
+// set up this device (otherwise no kernel can have written it).  Called by
+// vd_sync after it has waited for the stream; no allocation.
+vd_status vd_internal_noalloc_status(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(VD_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return VD_OK;
+    void *addr = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        addr = g_status_addr[dev];
+    }
+    if (!addr) return VD_OK;
+    int h = 0;
+    e = cudaMemcpy(&h, addr, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(VD_ECUDA, "cudaMemcpy (noalloc status): %s", cudaGetErrorString(e));
+    if (h) {
+        e = cudaMemset(addr, 0, sizeof h);
+        if (e != cudaSuccess) return fail(VD_ECUDA, "cudaMemset (noalloc status): %s", cudaGetErrorString(e));
+        return fail(VD_EBOUNDS, "a vd_decode_noalloc kernel refused a frame pair that would overrun "
+                                "its scratch (status 0x%x); its outputs were not written", h);
+    }
+    return VD_OK;
+}
+
 extern "C" int64_t vd_noalloc_scratch_limit(void) { return (int64_t)kNoallocScratchBytes; }
 
 extern "C" vd_status vd_decode_noalloc(const vd_code *c, const void *d_llr, int64_t n_info, int f,
@@ -88,7 +117,12 @@ extern "C" vd_status vd_decode_noalloc(const vd_code *c, const void *d_llr, int6
     if (radix != 2 && radix != 4) return fail(VD_EINVAL, "radix must be 2 or 4");
     if (flags & ~(uint32_t)(VD_TERMINATED | VD_START_UNKNOWN))
         return fail(VD_EINVAL, "unknown flag bits 0x%x", flags);
-    if (n_info == 0) return VD_OK;
+    if (n_info == 0) {
+        // a zero-length call only sets the device up (module load, symbol lookup)
+        void *scratch = nullptr;
+        int *status = nullptr;
+        return device_arrays(&scratch, &status);
+    }
     if (!d_llr || !d_out) return fail(VD_EINVAL, "NULL device pointer");
     if (f < n_info && f % 32 != 0)
         return fail(VD_EINVAL, "f=%d must be a multiple of 32 when the stream has several frames", f);
@@ -120,8 +154,7 @@ extern "C" vd_status vd_decode_noalloc(const vd_code *c, const void *d_llr, int6
     vd_status st = device_arrays(&scratch, &status);
     if (st != VD_OK) return st;
     cudaStream_t cs = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), cs);
-    if (e != cudaSuccess) return fail(VD_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    cudaError_t e;
 
     vd::StreamParams p;
     p.llr = (const int8_t *)d_llr;

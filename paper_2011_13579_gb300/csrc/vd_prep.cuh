@@ -1,6 +1,6 @@
 // Input pre-pass helper: expands transmitted (kept) LLR values to beta int8
-// LLRs per stage, inserting 0 at the positions a puncturing pattern erases
-// and sign-extending 4-bit values.  The kept values are stage-major with b
+// LLRs per stage, inserting 0 at the positions a puncturing pattern erases,
+// sign-extending 4-bit values and mapping hard decisions to +-1.  The kept values are stage-major with b
 // ascending, so the values of puncturing period g (stages g*period ..) start
 // at g * kept_per_period.
 //
@@ -15,11 +15,13 @@
 
 namespace vd {
 
-// One value of the kept stream (int8, or 4-bit two per byte, low nibble
-// first); 0 at or past n_kept (the end of this packet's values), which is
-// never read.
+// One value of the kept stream (int8; 4-bit two per byte, low nibble
+// first; or a hard decision, eight per byte, bit 0 first, mapped to +1 for
+// bit 0 and -1 for bit 1); 0 at or past n_kept (the end of this packet's
+// values), which is never read.
 __device__ __forceinline__ int8_t prep_kept_value(const uint8_t *src, int64_t k, int64_t n_kept, int llr_type) {
     if (k >= n_kept) return 0;
+    if (llr_type == VD_LLR_HARD) return ((src[k >> 3] >> (k & 7)) & 1u) ? (int8_t)-1 : (int8_t)1;
     if (llr_type == VD_LLR_S4) {
         const uint8_t byte = src[k >> 1];
         const uint8_t nib = (k & 1) ? (byte >> 4) : (byte & 0x0F);

@@ -219,7 +219,10 @@ bool launch_batch(vd_server *s, Slot &sl) {
         if (!r->prep_bytes) continue;
         vd::PrepJob &j = sl.h_jobs[n_jobs++];
         j.src = r->dev_llr;   // NULL: the values came up with the batch, into the region
-        j.src_off = r->dev_llr ? 0 : r->llr_type == VD_LLR_S4 ? (int64_t)(r->in_off * 2) : (int64_t)r->in_off;
+        j.src_off = r->dev_llr ? 0
+                    : r->llr_type == VD_LLR_S4   ? (int64_t)(r->in_off * 2)
+                    : r->llr_type == VD_LLR_HARD ? (int64_t)(r->in_off * 8)
+                                                 : (int64_t)r->in_off;
         j.dst_off = (int64_t)r->prep_off;
         j.T = r->T;
         j.code_slot = r->code_id;
@@ -524,7 +527,8 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
                         int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
     if (!s) return fail(VD_EINVAL, "server is NULL");
     if (code_id < 0 || code_id >= (int)s->codes.size()) return fail(VD_EINVAL, "bad code_id");
-    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4) return fail(VD_EUNSUPPORTED, "server takes int8 or 4-bit LLRs");
+    if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_HARD)
+        return fail(VD_EUNSUPPORTED, "server takes int8, 4-bit or hard-decision input");
     if (n_info <= 0 || n_info > s->cfg.max_packet_bits) return fail(VD_EINVAL, "n_info outside (0, max_packet_bits]");
     if (flags & ~(uint32_t)(VD_TERMINATED | VD_START_UNKNOWN)) return fail(VD_EINVAL, "unknown flags");
     const vd_code *c = s->codes[(size_t)code_id];
@@ -544,8 +548,10 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
     const int32_t F = k7 ? (s->cfg.f7 > 0 ? s->cfg.f7 : 256) : (s->cfg.f9 > 0 ? s->cfg.f9 : 512);
     r->f = n_info <= F ? (int32_t)n_info : F;
     r->v = k7 ? (s->cfg.v7 > 0 ? s->cfg.v7 : 42) : (s->cfg.v9 > 0 ? s->cfg.v9 : 64);
-    const size_t value_bytes = llr_type == VD_LLR_S4 ? (size_t)((kept + 1) / 2) : (size_t)kept;
-    r->prep_bytes = (c->punctured || llr_type == VD_LLR_S4) ? (size_t)(T * c->beta) : 0;
+    const size_t value_bytes = llr_type == VD_LLR_S4     ? (size_t)((kept + 1) / 2)
+                               : llr_type == VD_LLR_HARD ? (size_t)((kept + 7) / 8)
+                                                         : (size_t)kept;
+    r->prep_bytes = (c->punctured || llr_type != VD_LLR_S8) ? (size_t)(T * c->beta) : 0;
     r->out_words = (size_t)((n_info + 31) / 32);
     r->stage_off = r->stage_bytes = 0;
     if (device) {

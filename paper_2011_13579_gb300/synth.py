@@ -15,6 +15,7 @@ Conventions (the paper is silent on them):
   * noise: sigma = sqrt(1 / (2 R 10^(EbN0/10))) with R the nominal code rate
     after puncturing.  For R = 1/2 this is 10^(-EbN0/20); the printed formula
     in Sec. IX-B is garbled;
+  * hard decision = 1 where y < 0 (packed eight per byte, bit 0 first);
   * int8 LLR  = clip(rint(32 y), -127, 127);
     4-bit LLR = clip(rint(2 y), -7, 7), two per byte, low nibble first;
     fp16 LLR  = half(2 y / sigma^2); fp64 LLR = 2 y / sigma^2;
@@ -115,6 +116,17 @@ def llr_f64(y: np.ndarray, sigma: float) -> np.ndarray:
     return 2.0 * y / (sigma * sigma)
 
 
+def hard_decide(y: np.ndarray) -> np.ndarray:
+    """Hard decisions (Sec. II-C hard-decision mode): bit 1 where the sample
+    is negative (BPSK sends bit 0 as +1), as uint8 0/1."""
+    return (np.asarray(y) < 0.0).astype(np.uint8)
+
+
+def pack_hard(bits: np.ndarray) -> np.ndarray:
+    """Packs hard decisions eight per byte, earliest value in bit 0."""
+    return np.packbits(np.asarray(bits, dtype=np.uint8).reshape(-1), bitorder="little")
+
+
 @dataclass
 class Stream:
     """One received stream: info bits, and the kept (transmitted) samples."""
@@ -148,6 +160,10 @@ class Stream:
 
     def f64(self):
         return llr_f64(self.y, self.sigma)
+
+    def hard(self):
+        """Hard decisions of the kept samples, uint8 0/1 (unpacked)."""
+        return hard_decide(self.y)
 
 
 def make_stream(rng, K, gens, n_info, ebn0_db, terminated, pattern=None) -> Stream:

@@ -663,3 +663,70 @@ def test_f64_gap_and_max_metric_brute_force(K, gens, terminated, start_unknown):
                 gaps.append(abs(c[1] - c[0]))
             want_gap = min(gaps)
             assert gap[s] == pytest.approx(want_gap, rel=1e-9, abs=1e-9), (trial, s)
+
+
+# --------------------------------------------------- hard decisions (Sec. II-C)
+
+@pytest.mark.parametrize("K,gens", [(7, synth.K7_GENS), (5, (0o23, 0o35)), (4, (0o13, 0o15, 0o17))])
+@pytest.mark.parametrize("terminated", [False, True])
+@pytest.mark.parametrize("erasures", [False, True])
+def test_hard_decision_brute_force_min_distance(K, gens, terminated, erasures):
+    """Full-length hard-decision decoding returns a message whose codeword is
+    at the minimum Hamming distance from the received bits (over the
+    positions not erased), found by enumerating all 2^n messages; the
+    argmin itself when it is unique."""
+    code = oracle.Code(K, gens)
+    rng = np.random.Generator(np.random.PCG64(606 + K + 2 * terminated + 4 * erasures))
+    n = 12
+    T = oracle.n_stages(code, n, terminated)
+    msgs = _all_messages(n)
+    tx = msgs if not terminated else np.concatenate(
+        [msgs, np.zeros((msgs.shape[0], K - 1), np.uint8)], axis=1)
+    cw = _batch_encode(K, gens, tx)                                   # [M, T, beta]
+    for trial in range(6):
+        rx = rng.integers(0, 2, size=(T, code.beta)).astype(np.uint8)
+        if erasures:
+            rx[rng.random((T, code.beta)) < 0.4] = 2
+        dist = ((cw != rx[None]) & (rx[None] < 2)).sum(axis=(1, 2))
+        dec = oracle.unpack_bits(oracle.decode_hard(code, rx, n, f=n, v=K + n, terminated=terminated), n)
+        idx = int((dec.astype(np.int64) << np.arange(n)).sum())
+        assert dist[idx] == dist.min(), trial
+        if (dist == dist.min()).sum() == 1:
+            assert idx == int(np.argmin(dist))
+
+
+@pytest.mark.parametrize("pat", [None, synth.PUNCT_R23, synth.PUNCT_R34])
+def test_hard_decision_noiseless_and_segmented(pat):
+    """Received bits equal to the (punctured) codeword decode to the message,
+    full length and segmented (f=256, v=42)."""
+    rng = np.random.Generator(np.random.PCG64(607))
+    code = oracle.Code(7, synth.K7_GENS, puncture=pat)
+    n = 3000
+    bits = synth.random_bits(rng, n)
+    tx = np.concatenate([bits, np.zeros(6, np.uint8)])
+    cw = synth.conv_encode(7, synth.K7_GENS, tx)
+    T = cw.shape[0]
+    kept = cw[synth.puncture_mask(pat, T)] if pat is not None else cw.reshape(-1)
+    rx = oracle.depuncture_hard(code, kept, T)
+    want = oracle.pack_bits(bits)
+    assert np.array_equal(oracle.decode_hard(code, rx, n, f=n, v=n + 7, terminated=True), want)
+    assert np.array_equal(oracle.decode_hard(code, rx, n, f=256, v=42, terminated=True), want)
+    if pat is not None:
+        assert np.all(rx[~synth.puncture_mask(pat, T)] == 2)
+
+
+def test_hard_decision_equals_unit_llr_correlation():
+    """Minimising the Hamming distance is maximising the correlation with
+    +-1 LLRs (Eq. BM gives beta - 2 d per unerased stage): the hard-decision
+    decode equals the soft decode of the same decisions as LLRs +1 / -1 / 0
+    (erased), frame by frame, including the tie rules."""
+    rng = np.random.Generator(np.random.PCG64(608))
+    code = oracle.Code(7, synth.K7_GENS, puncture=synth.PUNCT_R34)
+    n = 4000
+    st = synth.make_stream(rng, 7, synth.K7_GENS, n, 1.0, True, pattern=synth.PUNCT_R34)
+    rx = oracle.depuncture_hard(code, st.hard(), st.T)
+    llr = np.where(rx == 2, 0, 1 - 2 * rx.astype(np.int32)).astype(np.int32)
+    for f, v in ((256, 42), (64, 6), (n, n + 7)):
+        a = oracle.decode_hard(code, rx, n, f=f, v=v, terminated=True)
+        b = oracle.decode(code, llr, n, f=f, v=v, terminated=True)
+        assert np.array_equal(a, b), (f, v)
