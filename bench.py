@@ -446,15 +446,40 @@ def run_packets(args, dev, s):
     for x in side:
         vd.vd_sync(x)
     identical = bool(torch.equal(out_b, out_p))
+
+    # the same per-packet calls issued by the library's C loop (vd_decode_each)
+    pk_each = dict(pk)
+    pk_each["f"] = np.asarray(f, np.int32)
+    pk_each["v"] = np.asarray(v, np.int32)
+    out_c = torch.full((nw,), -1, dtype=torch.int32, device=dev)
+    vd.vd_decode_each(codes, pk_each, llr, out_c, radix, side)   # warm-up (scratch already sized)
+    torch.cuda.synchronize(dev)
+    a.record(s)
+    for x in side:
+        x.wait_event(a)
+    vd.vd_decode_each(codes, pk_each, llr, out_c, radix, side)
+    for x in side:
+        e = torch.cuda.Event()
+        e.record(x)
+        s.wait_event(e)
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    ms_c = a.elapsed_time(b)
+    for x in side:
+        vd.vd_sync(x)
+    identical_c = bool(torch.equal(out_b, out_c))
     plan.close()
     return {"workload": f"{n} terminated K=7 packets, log-uniform 96..12000 info bits, r1/2 r2/3 r3/4 "
                         "equal shares, Eb/N0 U(2,7) dB, int8 kept LLRs",
             "info_bits": bits, "batched_gbps": bits / (ms_b / 1e3) / 1e9, "batched_ms": ms_b,
             "plain_gbps": bits / (ms_p / 1e3) / 1e9, "plain_ms": ms_p, "speedup": ms_p / ms_b,
             "identical_output": identical,
+            "plain_c_loop_gbps": bits / (ms_c / 1e3) / 1e9, "plain_c_loop_ms": ms_c,
+            "speedup_vs_c_loop": ms_c / ms_b, "identical_output_c_loop": identical_c,
             "batched_form": "one persistent launch per step (autotuned plan, CUDA-graph replay)",
             "plain_form": f"one vd_decode call per packet, same f/v/radix, round-robin over {PLAIN_STREAMS} "
-                          "CUDA streams (as many hardware queues), issued from Python via ctypes",
+                          "CUDA streams (as many hardware queues), issued from Python via ctypes; "
+                          "plain_c_loop: the same calls issued by the library's C loop (vd_decode_each)",
             "tune": {"radix": radix, "lanes": int(info.lanes), "resident_warps": int(info.resident_warps),
                      "f_median": int(np.median(f)), "v_median": int(np.median(v))}}
 

@@ -231,6 +231,19 @@ vd_status vd_batch_plan_status(vd_batch_plan *plan, void *stream);
 /* Frees a plan after the device is idle (NULL is ignored). */
 void vd_batch_plan_destroy(vd_batch_plan *plan);
 
+/*
+ * vd_decode_each — the plain form a batch is measured against: one vd_decode
+ * call (one or two launches) per packet, issued from C in packet order and
+ * spread round-robin over n_streams caller streams.  Each packet's f and v
+ * must be set (f > 0), e.g. from vd_batch_plan_packet_tune, so that the bits
+ * equal the batch's.  Offsets and arenas as in vd_batch_plan_launch.
+ * Asynchronous; the first failing call's status is returned and later
+ * packets are not launched.
+ */
+vd_status vd_decode_each(const vd_code *const *codes, int n_codes, const vd_packet *packets,
+                         int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena, int radix,
+                         void *const *streams, int n_streams);
+
 /* One-shot batch decode: plan, launch, wait for `stream`, free. */
 vd_status vd_decode_batch(const vd_code *const *codes, int n_codes, const vd_packet *packets,
                           int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena,
@@ -425,6 +438,35 @@ vd_status vd_decode_noalloc(const vd_code *code, const void *d_llr, int64_t n_in
 
 /* Size in bytes of the fixed survivor scratch used by vd_decode_noalloc. */
 int64_t vd_noalloc_scratch_limit(void);
+
+/*
+ * vd_transmit — the transmitter and channel of the paper's verification
+ * system (Sec. IX-B) on the GPU, a source of received values that never
+ * touches the host: information bits -> convolutional encoder from state 0
+ * (Sec. II-A; k-1 zero tail bits when flags has VD_TERMINATED) -> the code's
+ * puncturing (kept positions, stage-major, b ascending) -> BPSK (bit 0 ->
+ * +1, bit 1 -> -1) -> AWGN y = x + sigma z -> quantiser of llr_type:
+ *   VD_LLR_S8: clip(rint(32 y), -127, 127)     VD_LLR_S4: clip(rint(2 y), -7, 7), packed
+ *   VD_LLR_F16: half(2 y / sigma^2)            VD_LLR_HARD: y < 0, packed
+ * z of the k-th kept value is standard normal number k of the stream:
+ * Philox4x64-10 (Salmon et al., SC 2011) with key (seed, stream_id) on
+ * counter (k / 4, 0, 0, 0), four normals per counter by the Box-Muller
+ * transform (words 0,1 and 2,3: u = ((w >> 11) + 1) 2^-53; sqrt(-2 ln u)
+ * cos(2 pi v), sqrt(-2 ln u) sin(2 pi v)) in double precision.  The same
+ * (seed, stream_id) give the same samples on every call.
+ *   d_bits:  ceil(n_info/32) device words of information bits, LSB-first.
+ *   sigma:   noise standard deviation >= 0 (> 0 for VD_LLR_F16); for Eb/N0
+ *            in dB and code rate R, sigma = sqrt(1 / (2 R 10^(EbN0/10))).
+ *   d_out:   vd_transmit_bytes() bytes of device memory (written).
+ * Asynchronous on stream.  VD_EINVAL on bad arguments, VD_ECUDA on launch
+ * failure.
+ */
+vd_status vd_transmit(const vd_code *code, const uint32_t *d_bits, int64_t n_info, uint32_t flags,
+                      double sigma, uint64_t seed, uint64_t stream_id, int llr_type, void *d_out,
+                      void *stream);
+
+/* Bytes vd_transmit writes for these arguments (-1 on bad arguments). */
+int64_t vd_transmit_bytes(const vd_code *code, int64_t n_info, uint32_t flags, int llr_type);
 
 /* Number of frames of a stream decode: ceil(n_info / f) (0 if n_info <= 0). */
 int64_t vd_num_frames(int64_t n_info, int f);

@@ -94,12 +94,25 @@ def _load():
         lib.or_decode_frames_i64.restype = ctypes.c_int
         lib.or_decode_hard.argtypes = [P(_Code), P(u8), i64, ctypes.c_int, ctypes.c_int, i64, i64, P(u32)]
         lib.or_decode_hard.restype = ctypes.c_int
+        u64 = ctypes.c_uint64
+        lib.or_philox4x64.argtypes = [P(u64), P(u64), P(u64)]
+        lib.or_philox4x64.restype = None
+        lib.or_transmit.argtypes = [P(_Code), P(u8), i64, ctypes.c_int, dbl, u64, u64, P(dbl), i64]
+        lib.or_transmit.restype = i64
+        lib.or_decode_packets_i64.argtypes = [P(_Code), P(_Packet), i64, P(ctypes.c_int8), P(u32), ctypes.c_int]
+        lib.or_decode_packets_i64.restype = ctypes.c_int
         _lib = lib
         return lib
 
 
 def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class _Packet(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("terminated", ctypes.c_int32), ("start_unknown", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("kept_off", ctypes.c_int64), ("n_info", ctypes.c_int64),
+                ("f", ctypes.c_int64), ("v", ctypes.c_int64), ("out_word_off", ctypes.c_int64)]
 
 
 class Code:
@@ -201,6 +214,32 @@ def decode_full(code: Code, llr, n_info: int, terminated=False, start_unknown=Fa
                   terminated=terminated, start_unknown=start_unknown)
 
 
+def decode_packets(codes, code_id, kept_off, n_info, f, v, terminated, start_unknown, out_word_off,
+                   arena_s8, n_words, threads: int = 1):
+    """Decodes a batch of packets (decode() per packet, after depuncturing
+    its kept int8 values from ``arena_s8``), spread over host threads.
+    Returns the packed output words (n_words)."""
+    lib = _load()
+    n = len(n_info)
+    cs = (_Code * max(len(codes), 1))(*[c._c for c in codes])
+    pk = (_Packet * max(n, 1))()
+    for i in range(n):
+        pk[i].code = int(code_id[i])
+        pk[i].terminated = int(bool(terminated[i]))
+        pk[i].start_unknown = int(bool(start_unknown[i]))
+        pk[i].kept_off = int(kept_off[i])
+        pk[i].n_info = int(n_info[i])
+        pk[i].f = int(f[i])
+        pk[i].v = int(v[i])
+        pk[i].out_word_off = int(out_word_off[i])
+    arena = np.ascontiguousarray(arena_s8, dtype=np.int8)
+    out = np.zeros(max(int(n_words), 1), dtype=np.uint32)
+    rc = lib.or_decode_packets_i64(cs, pk, n, _ptr(arena, ctypes.c_int8), _ptr(out, ctypes.c_uint32), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle decode_packets failed ({rc})")
+    return out[: int(n_words)]
+
+
 def decode_f64(code: Code, llr, n_info: int, f: int, v: int, terminated=False,
                start_unknown=False, threads: int = 1):
     """Segmented decode in fp64.  Returns (packed words, min_gap[nwin], max_abs_pm[nwin])."""
@@ -245,6 +284,47 @@ def decode_hard(code: Code, rx, n_info: int, f: int, v: int, terminated=False, s
     if rc != 0:
         raise RuntimeError(f"oracle decode_hard failed ({rc})")
     return out[: (n_info + 31) // 32]
+
+
+def philox4x64(counter, key):
+    """Philox4x64-10 of a 4-word counter and a 2-word key -> 4 uint64 words."""
+    lib = _load()
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib.or_philox4x64(_ptr(c, ctypes.c_uint64), _ptr(k, ctypes.c_uint64), _ptr(out, ctypes.c_uint64))
+    return out
+
+
+def transmit(code: Code, bits, n_info: int, terminated: bool, sigma: float, seed: int, stream_id: int = 0):
+    """Received samples y (float64, kept positions only) of the verification
+    system (Sec. IX-B): encoder -> puncture -> BPSK -> AWGN with Philox4x64-10
+    normals (key = (seed, stream_id), counter block k // 4 for value k)."""
+    lib = _load()
+    b = np.ascontiguousarray(bits, dtype=np.uint8)
+    T = n_stages(code, n_info, terminated)
+    y = np.zeros(max(code.n_kept(T), 1), dtype=np.float64)
+    n = lib.or_transmit(ctypes.byref(code._c), _ptr(b, ctypes.c_uint8), n_info, int(bool(terminated)),
+                        float(sigma), int(seed) & (2**64 - 1), int(stream_id) & (2**64 - 1),
+                        _ptr(y, ctypes.c_double), y.size)
+    if n < 0:
+        raise RuntimeError("oracle transmit failed")
+    return y[:n]
+
+
+def quantise(y, llr_type: str, sigma: float = 1.0):
+    """The quantisers of the received samples: 's8' clip(rint(32 y), +-127),
+    's4' clip(rint(2 y), +-7), 'f16' half(2 y / sigma^2), 'hard' (y < 0)."""
+    y = np.asarray(y, dtype=np.float64)
+    if llr_type == "s8":
+        return np.clip(np.rint(32.0 * y), -127, 127).astype(np.int8)
+    if llr_type == "s4":
+        return np.clip(np.rint(2.0 * y), -7, 7).astype(np.int8)
+    if llr_type == "f16":
+        return (2.0 * y / (sigma * sigma)).astype(np.float16)
+    if llr_type == "hard":
+        return (y < 0.0).astype(np.uint8)
+    raise ValueError(llr_type)
 
 
 def decode_frames(code: Code, llr, n_info: int, f: int, v: int, frames, terminated=False,

@@ -52,6 +52,10 @@
 #include <pthread.h>
 #include <math.h>
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 #define OR_MAX_BETA 4
 #define OR_MAX_PERIOD 8
 #define OR_NEG_INF_I64 (INT64_MIN / 4)
@@ -619,4 +623,165 @@ int or_decode_hard(const or_code *c, const uint8_t *rx, int64_t n_info, int term
     or_pack_bits(bits, n_info, out);
     free(bits); free(d); free(dn); free(phi);
     return 0;
+}
+
+/* ------------------------------------ transmitter and channel, Sec. IX-B */
+
+/*
+ * Philox4x64-10, the counter-based generator of Salmon, Moraes, Dror and
+ * Shaw ("Parallel random numbers: as easy as 1, 2, 3", SC 2011), written
+ * from its published definition: ten rounds, each multiplying counter words
+ * 0 and 2 by two fixed 64-bit constants into 128-bit products and mixing
+ * the halves with counter words 1 and 3 and the key; the key is bumped by
+ * two Weyl constants between rounds.
+ */
+static void or_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    const uint64_t a0 = a & 0xFFFFFFFFu, a1 = a >> 32, b0 = b & 0xFFFFFFFFu, b1 = b >> 32;
+    const uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+    const uint64_t mid = (p00 >> 32) + (p01 & 0xFFFFFFFFu) + (p10 & 0xFFFFFFFFu);
+    *lo = (mid << 32) | (p00 & 0xFFFFFFFFu);
+    *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+void or_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
+{
+    uint64_t c[4] = { ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3] };
+    uint64_t k[2] = { key_in[0], key_in[1] };
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        or_mulhilo64(0xD2E7470EE14C6C93ull, c[0], &hi0, &lo0);
+        or_mulhilo64(0xCA5A826395121157ull, c[2], &hi1, &lo1);
+        const uint64_t n0 = hi1 ^ c[1] ^ k[0], n1 = lo1, n2 = hi0 ^ c[3] ^ k[1], n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        if (r < 9) { k[0] += 0x9E3779B97F4A7C15ull; k[1] += 0xBB67AE8584CAA73Bull; }
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* Uniform in (0, 1] from the top 53 bits of a 64-bit word. */
+static double or_unit(uint64_t x) { return (double)((x >> 11) + 1u) * 0x1.0p-53; }
+
+/*
+ * The four standard normals of counter block q of a stream: Philox4x64-10
+ * with key (seed, stream_id) and counter (q, 0, 0, 0), turned into normals
+ * by the Box-Muller transform on word pairs (0, 1) and (2, 3):
+ * sqrt(-2 ln u) cos(2 pi v), sqrt(-2 ln u) sin(2 pi v).
+ */
+static void or_normals4(uint64_t seed, uint64_t stream_id, uint64_t q, double z[4])
+{
+    const uint64_t ctr[4] = { q, 0, 0, 0 }, key[2] = { seed, stream_id };
+    uint64_t w[4];
+    or_philox4x64(ctr, key, w);
+    for (int p = 0; p < 2; ++p) {
+        const double u = or_unit(w[2 * p]), v = or_unit(w[2 * p + 1]);
+        const double rad = sqrt(-2.0 * log(u)), ang = 2.0 * M_PI * v;
+        z[2 * p] = rad * cos(ang);
+        z[2 * p + 1] = rad * sin(ang);
+    }
+}
+
+/*
+ * Transmitter and channel of the verification system (Sec. IX-B): the
+ * information bits (one per byte) go through the encoder from state 0
+ * (Sec. II-A, with k-1 zero tail bits when terminated), the puncturing
+ * pattern keeps the transmitted positions (stage-major, b ascending), BPSK
+ * maps bit 0 to +1 and 1 to -1, and AWGN adds sigma times the k-th normal
+ * of the stream to the k-th kept value.  Writes the n_kept received samples
+ * y (double) and returns n_kept, or -1.  Quantisation is the caller's.
+ */
+int64_t or_transmit(const or_code *c, const uint8_t *bits, int64_t n_info, int terminated, double sigma,
+                    uint64_t seed, uint64_t stream_id, double *y, int64_t y_cap)
+{
+    if (or_check_code(c) || n_info < 0) return -1;
+    const int64_t T = n_info + (terminated ? c->K - 1 : 0);
+    uint8_t *in = (uint8_t *)calloc((size_t)(T > 0 ? T : 1), 1);
+    uint8_t *cw = (uint8_t *)malloc((size_t)(T > 0 ? T : 1) * (size_t)c->beta);
+    if (!in || !cw) { free(in); free(cw); return -1; }
+    for (int64_t t = 0; t < n_info; ++t) in[t] = bits[t] & 1u;
+    or_encode(c, in, T, cw);
+    int64_t k = 0;
+    double z[4];
+    for (int64_t t = 0; t < T; ++t) {
+        const int ph = (int)(t % c->period);
+        for (int b = 0; b < c->beta; ++b) {
+            if (!c->punct[b][ph]) continue;
+            if (k >= y_cap) { free(in); free(cw); return -1; }
+            if ((k & 3) == 0) or_normals4(seed, stream_id, (uint64_t)k >> 2, z);
+            y[k] = (cw[t * c->beta + b] ? -1.0 : 1.0) + sigma * z[k & 3];
+            ++k;
+        }
+    }
+    free(in); free(cw);
+    return k;
+}
+
+/* ------------------------------------------------ many packets, int64 */
+
+/* One packet of a batch: its code, where its kept int8 values start in the
+ * arena, its length and flags, the frame length and overlap to decode it
+ * with, and where its packed output words go. */
+typedef struct {
+    int32_t code;
+    int32_t terminated, start_unknown;
+    int32_t pad;
+    int64_t kept_off, n_info, f, v, out_word_off;
+} or_packet;
+
+typedef struct {
+    const or_code *codes;
+    const or_packet *pk;
+    int64_t n_packets;
+    const int8_t *arena;
+    uint32_t *out;
+    int nthreads, tid, status;
+} or_batch_job;
+
+static void *or_batch_worker(void *arg)
+{
+    or_batch_job *J = (or_batch_job *)arg;
+    int32_t *kept = NULL, *full = NULL;
+    int64_t cap_kept = 0, cap_full = 0;
+    for (int64_t i = J->tid; i < J->n_packets; i += J->nthreads) {
+        const or_packet *p = &J->pk[i];
+        const or_code *c = &J->codes[p->code];
+        const int64_t T = p->n_info + (p->terminated ? c->K - 1 : 0);
+        int64_t n_kept = 0;
+        for (int64_t t = 0; t < T; ++t)
+            for (int b = 0; b < c->beta; ++b) n_kept += c->punct[b][t % c->period] != 0;
+        if (n_kept > cap_kept) { free(kept); cap_kept = n_kept; kept = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap_kept); }
+        if (T * c->beta > cap_full) { free(full); cap_full = T * c->beta; full = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap_full); }
+        if (!kept || !full) { J->status = -2; break; }
+        for (int64_t k = 0; k < n_kept; ++k) kept[k] = J->arena[p->kept_off + k];
+        if (or_depuncture_i32(c, kept, n_kept, T, full) < 0) { J->status = -1; break; }
+        const int rc = or_decode_i64(c, full, p->n_info, p->terminated, p->start_unknown, p->f, p->v,
+                                     J->out + p->out_word_off, NULL, 1);
+        if (rc) { J->status = rc; break; }
+    }
+    free(kept); free(full);
+    return NULL;
+}
+
+/*
+ * Decodes every packet of a batch with or_decode_i64 (Algorithms 1 and 2
+ * over the frames of Sec. III, after depuncturing), packets spread over
+ * nthreads host threads.  arena: the kept int8 values of all packets.
+ */
+int or_decode_packets_i64(const or_code *codes, const or_packet *pk, int64_t n_packets, const int8_t *arena,
+                          uint32_t *out, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n_packets) nthreads = (int)(n_packets > 0 ? n_packets : 1);
+    or_batch_job *jobs = (or_batch_job *)calloc((size_t)nthreads, sizeof(or_batch_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int i = 0; i < nthreads; ++i) {
+        or_batch_job J = { codes, pk, n_packets, arena, out, nthreads, i, 0 };
+        jobs[i] = J;
+    }
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, or_batch_worker, &jobs[i]);
+    int rc = 0;
+    for (int i = 0; i < nthreads; ++i) { pthread_join(th[i], NULL); if (jobs[i].status) rc = jobs[i].status; }
+    free(jobs); free(th);
+    return rc;
 }

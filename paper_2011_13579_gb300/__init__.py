@@ -25,7 +25,7 @@ __all__ = [
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_int_peak", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_decode_each", "vd_int_peak", "vd_transmit", "vd_transmit_bytes", "transmit", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -159,8 +159,14 @@ def lib():
         L.vd_get_tune.restype = i32
         L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
         L.vd_bm_gate.restype = i32
+        L.vd_decode_each.argtypes = [P(vp), i32, P(VdPacket), i64, vp, vp, i32, P(vp), i32]
+        L.vd_decode_each.restype = i32
         L.vd_int_peak.argtypes = [i32, i64, i32, vp, vp, vp]
         L.vd_int_peak.restype = i32
+        L.vd_transmit.argtypes = [vp, vp, i64, u32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, i32, vp, vp]
+        L.vd_transmit.restype = i32
+        L.vd_transmit_bytes.argtypes = [vp, i64, u32, i32]
+        L.vd_transmit_bytes.restype = i64
         L.vd_sync.argtypes = [vp]
         L.vd_sync.restype = i32
         L.vd_release_scratch.argtypes = []
@@ -246,12 +252,49 @@ def vd_bm_gate(variant, llr_words, n_pairs, n_stages, checksum, metrics=None, st
                             _stream_handle(stream)))
 
 
+def vd_decode_each(codes, packets, llr_arena, out_arena, radix, streams) -> None:
+    """One vd_decode per packet from C (packets: VdPacket array or dict with
+    f > 0 per packet), round-robin over ``streams`` (torch streams)."""
+    arr, n = _packet_array(packets)
+    sh = (ctypes.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
+    _check(lib().vd_decode_each(_code_handles(codes), len(codes), arr, n, ctypes.c_void_p(llr_arena.data_ptr()),
+                                ctypes.c_void_p(out_arena.data_ptr()), int(radix), sh, len(streams)))
+
+
 def vd_int_peak(variant, iters, n_blocks, cycles, sink, stream=None) -> None:
     """Integer-issue microbenchmark on device tensors: cycles (int64
     [n_blocks]) receives each block's SM-clock span, sink (int32
     [n_blocks * 1024]) the folded chains."""
     _check(lib().vd_int_peak(int(variant), int(iters), int(n_blocks), ctypes.c_void_p(cycles.data_ptr()),
                              ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream)))
+
+
+def vd_transmit(handle, bits, n_info, flags, sigma, seed, stream_id, llr_type, out, stream=None) -> None:
+    """GPU transmitter and channel on device tensors: ``bits`` (packed info
+    words), ``out`` (vd_transmit_bytes() bytes)."""
+    _check(lib().vd_transmit(ctypes.c_void_p(handle), ctypes.c_void_p(bits.data_ptr()) if n_info else None,
+                             int(n_info), int(flags), float(sigma), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                             ctypes.c_uint64(int(stream_id) & (2**64 - 1)), int(llr_type),
+                             ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+
+def vd_transmit_bytes(handle, n_info, flags, llr_type) -> int:
+    n = int(lib().vd_transmit_bytes(ctypes.c_void_p(handle), int(n_info), int(flags), int(llr_type)))
+    if n < 0:
+        raise VdError(VD_EINVAL, "vd_transmit_bytes: bad arguments")
+    return n
+
+
+def transmit(code, bits_words, n_info, sigma, seed, stream_id=0, terminated=False, llr_type=VD_LLR_S8,
+             stream=None):
+    """Allocates the received-value buffer (torch uint8, on the bits' device)
+    and fills it with vd_transmit."""
+    import torch
+    flags = VD_TERMINATED if terminated else 0
+    nb = vd_transmit_bytes(code.handle, n_info, flags, llr_type)
+    out = torch.empty(max(nb, 1), dtype=torch.uint8, device=bits_words.device)
+    vd_transmit(code.handle, bits_words, n_info, flags, sigma, seed, stream_id, llr_type, out, stream)
+    return out[:nb]
 
 
 def vd_get_tune(handle, llr_type, f, v, radix) -> "VdTune":

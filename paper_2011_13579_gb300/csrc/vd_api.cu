@@ -503,6 +503,35 @@ extern "C" vd_status vd_decode(const vd_code *c, const void *d_llr, int llr_type
     return VD_OK;
 }
 
+extern "C" vd_status vd_decode_each(const vd_code *const *codes, int n_codes, const vd_packet *packets,
+                                    int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena, int radix,
+                                    void *const *streams, int n_streams) {
+    if (!codes || n_codes <= 0 || (n_packets > 0 && !packets) || n_packets < 0)
+        return fail(VD_EINVAL, "vd_decode_each: bad code or packet arrays");
+    if (!streams || n_streams <= 0) return fail(VD_EINVAL, "vd_decode_each: no streams");
+    for (int64_t i = 0; i < n_packets; ++i) {
+        const vd_packet &p = packets[i];
+        if (p.code_id < 0 || p.code_id >= n_codes || !codes[p.code_id])
+            return fail(VD_EINVAL, "vd_decode_each: packet %lld has a bad code_id", (long long)i);
+        if (p.f <= 0) return fail(VD_EINVAL, "vd_decode_each: packet %lld needs f > 0", (long long)i);
+        int64_t byte_off = p.llr_offset;
+        if (p.llr_type == VD_LLR_S4) {
+            if (p.llr_offset & 1) return fail(VD_EINVAL, "vd_decode_each: 4-bit packet %lld not on a byte", (long long)i);
+            byte_off = p.llr_offset / 2;
+        } else if (p.llr_type == VD_LLR_HARD) {
+            if (p.llr_offset & 7) return fail(VD_EINVAL, "vd_decode_each: hard packet %lld not on a byte", (long long)i);
+            byte_off = p.llr_offset / 8;
+        } else if (p.llr_type == VD_LLR_F16) {
+            byte_off = p.llr_offset * 2;
+        }
+        const vd_status st = vd_decode(codes[p.code_id], (const uint8_t *)d_llr_arena + byte_off, p.llr_type,
+                                       p.n_info, p.f, p.v, radix, p.flags, d_out_arena + p.out_word_offset,
+                                       nullptr, nullptr, streams[i % n_streams]);
+        if (st != VD_OK) return st;
+    }
+    return VD_OK;
+}
+
 extern "C" vd_status vd_get_tune(const vd_code *c, int llr_type, int f, int v, int radix, vd_tune *out) {
     if (!c || !out) return fail(VD_EINVAL, "NULL argument");
     if (f <= 0 || v < 0) return fail(VD_EINVAL, "f must be positive and v >= 0");

@@ -730,3 +730,67 @@ def test_hard_decision_equals_unit_llr_correlation():
         a = oracle.decode_hard(code, rx, n, f=f, v=v, terminated=True)
         b = oracle.decode(code, llr, n, f=f, v=v, terminated=True)
         assert np.array_equal(a, b), (f, v)
+
+
+# ------------------------------------------- transmitter and channel (Sec. IX-B)
+
+@pytest.mark.parametrize("seed,sid", [(0, 0), (1, 2), (2011135790, 7), (2**64 - 1, 2**63 + 5)])
+def test_philox4x64_matches_numpy(seed, sid):
+    """The oracle's Philox4x64-10 equals NumPy's Philox bit generator, which
+    advances its 256-bit counter before each block (so NumPy counter q - 1
+    yields block q; q = 0 wraps around from all ones)."""
+    for q in (0, 1, 2, 3, 1000, 2**40 + 3):
+        prev = (q - 1) % 2**256
+        ctr = np.array([(prev >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+        bg = np.random.Philox(key=np.array([seed, sid], dtype=np.uint64), counter=ctr)
+        assert np.array_equal(oracle.philox4x64([q, 0, 0, 0], [seed, sid]), bg.random_raw(4)), q
+
+
+@pytest.mark.parametrize("K,gens,pat,terminated", [(7, synth.K7_GENS, None, False), (7, synth.K7_GENS, "r23", True),
+                                                   (7, synth.K7_GENS, "r34", True), (9, synth.K9_GENS, None, True)])
+def test_transmit_noiseless_is_bpsk_of_the_codeword(K, gens, pat, terminated):
+    """sigma = 0: the received samples are the BPSK symbols (bit 0 -> +1) of
+    the punctured codeword of this file's independent encoder."""
+    pattern = {None: None, "r23": synth.PUNCT_R23, "r34": synth.PUNCT_R34}[pat]
+    code = oracle.Code(K, gens, puncture=pattern)
+    rng = np.random.Generator(np.random.PCG64(700 + K))
+    n = 1001
+    bits = synth.random_bits(rng, n)
+    tx = bits if not terminated else np.concatenate([bits, np.zeros(K - 1, np.uint8)])
+    cw = synth.conv_encode(K, gens, tx)
+    kept = cw[synth.puncture_mask(pattern, cw.shape[0])] if pattern is not None else cw.reshape(-1)
+    y = oracle.transmit(code, bits, n, terminated, 0.0, seed=5)
+    assert np.array_equal(y, 1.0 - 2.0 * kept.astype(np.float64))
+
+
+def test_transmit_noise_is_standard_normal():
+    """y - x over 400k samples is standard normal (Kolmogorov-Smirnov), and
+    the samples do not depend on sigma except through the scale."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    code = oracle.Code(7, synth.K7_GENS)
+    rng = np.random.Generator(np.random.PCG64(701))
+    n = 200_000
+    bits = synth.random_bits(rng, n)
+    x = oracle.transmit(code, bits, n, False, 0.0, seed=11, stream_id=3)
+    y = oracle.transmit(code, bits, n, False, 0.7, seed=11, stream_id=3)
+    z = (y - x) / 0.7
+    assert abs(z.mean()) < 5.0 / np.sqrt(z.size) and abs(z.var() - 1.0) < 5.0 * np.sqrt(2.0 / z.size)
+    assert scipy_stats.kstest(z, "norm").pvalue > 1e-4
+    y2 = oracle.transmit(code, bits, n, False, 1.4, seed=11, stream_id=3)
+    assert np.allclose((y2 - x) / 1.4, z, rtol=0, atol=1e-12)
+    other = oracle.transmit(code, bits, n, False, 0.7, seed=11, stream_id=4)
+    assert not np.array_equal(other, y)
+
+
+def test_quantisers_match_the_synthetic_recipe():
+    """The oracle's quantisers equal the input generator's (an independent
+    implementation of the same recipe)."""
+    rng = np.random.Generator(np.random.PCG64(702))
+    y = rng.normal(0.0, 3.0, size=50_000)
+    y[:8] = [0.0, -0.0, 1.0 / 64, -1.0 / 64, 0.25, -0.75, 200.0, -200.0]
+    sigma = 0.8
+    assert np.array_equal(oracle.quantise(y, "s8"), synth.quantise_s8(y))
+    assert np.array_equal(oracle.quantise(y, "s4"), synth.quantise_s4(y))
+    assert np.array_equal(oracle.quantise(y, "f16", sigma).view(np.uint16),
+                          synth.llr_f64(y, sigma).astype(np.float16).view(np.uint16))
+    assert np.array_equal(oracle.quantise(y, "hard"), synth.hard_decide(y))
