@@ -267,72 +267,29 @@ def run_gpu(args, rank, world):
     bits_per_step = N_INFO * len(streams)
     ms, value = whole_job_value(ms, bits_per_step, args.steps, world, dev)
 
-    # end to end through the public API with host buffers: pinned H2D of the
-    # step's LLRs, decode, D2H of the decoded words, all inside the timed
-    # region.  The batch path pipelines: the streams are split into parts, each
-    # decoded by its own plan; part j's upload overlaps part j-1's decode (two
-    # decode streams, so one plan's last tasks overlap the next plan's first),
-    # and each part's words go back as soon as it is decoded.
+    # end to end through the C ABI with host buffers: vd_decode_host uploads
+    # each stream from pinned host memory, decodes it (the persistent batch
+    # kernel, two decode streams) and downloads its words, all inside the timed
+    # region; stream i+1's upload overlaps stream i's decode.
     host_in = [torch.from_numpy(x).pin_memory() for x in streams]
     host_out = [torch.empty(nw, dtype=torch.int32).pin_memory() for _ in streams]
     e2e_steps = max(1, min(args.steps, 5))
-    parts = []
-    if plan is not None:
-        per = -(-len(streams) // max(1, args.e2e_parts))
-        for first in range(0, len(streams), per):
-            cnt = min(per, len(streams) - first)
-            parts.append((list(range(first, first + cnt)),   # same kernel shape as the timed plan
-                          stream_plan(vd, code, cnt, shape["radix"], shape["lanes"], s, first=first)))
-    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    comp = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    radix_e2e = shape["radix"]
+    vd.vd_decode_host(code.handle, host_in, N_INFO, F, V, radix_e2e, flags, host_out, stream=s)   # set-up
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s)
-    if parts:
-        for x in [up, down] + comp:
-            x.wait_event(e0)
-        done_prev = [None] * len(parts)
-        for _ in range(e2e_steps):
-            for j, (idx, pl) in enumerate(parts):
-                if done_prev[j] is not None:
-                    up.wait_event(done_prev[j])        # the previous step's decode read these inputs
-                with torch.cuda.stream(up):
-                    for i in idx:
-                        llr_dev[i].copy_(host_in[i], non_blocking=True)
-                ev_in = torch.cuda.Event()
-                ev_in.record(up)
-                cs = comp[j % 2]
-                cs.wait_event(ev_in)
-                pl.launch(arena, out_arena, stream=cs)
-                ev_done = torch.cuda.Event()
-                ev_done.record(cs)
-                done_prev[j] = ev_done
-                down.wait_event(ev_done)
-                with torch.cuda.stream(down):
-                    for i in idx:
-                        host_out[i].copy_(outs[i], non_blocking=True)
-        for x in [up, down] + comp:
-            ev = torch.cuda.Event()
-            ev.record(x)
-            s.wait_event(ev)
-    else:
-        with torch.cuda.stream(s):
-            for _ in range(e2e_steps):
-                for i in range(len(streams)):
-                    llr_dev[i].copy_(host_in[i], non_blocking=True)
-                for i in range(launches_per_step):
-                    one_launch(i)
-                for i in range(len(streams)):
-                    host_out[i].copy_(outs[i], non_blocking=True)
+    for _ in range(e2e_steps):
+        vd.vd_decode_host(code.handle, host_in, N_INFO, F, V, radix_e2e, flags, host_out, stream=s)
     e1.record(s)
     torch.cuda.synchronize(dev)
+    vd.vd_sync(s)
     e2e_ms = e0.elapsed_time(e1)
-    for _, pl in parts:
-        pl.close()
     e2e_value = bits_per_step * e2e_steps / (e2e_ms / 1e3) / 1e9
     h2d = sum(int(x.size) for x in streams)
     d2h = nw * 4 * len(streams)
+    e2e_same = all(torch.equal(host_out[i], outs[i].cpu()) for i in range(len(streams)))
 
     # sanity: the decode of the 6 dB stream is nearly error-free
     dec = outs[-1].cpu().numpy().view(np.uint32)
@@ -361,9 +318,9 @@ def run_gpu(args, rank, world):
             "words_r2": words_r2, "words_r4": words_r4,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h),
-                    "form": (f"{len(parts)} batch plans; pinned uploads overlap decoding on two streams"
-                             if parts else "upload, decode, download in order on one stream")},
+                    "d2h_bytes_per_step": int(d2h), "same_bits_as_device_run": bool(e2e_same),
+                    "form": "one vd_decode_host call per step (C ABI, pinned host buffers): per stream an "
+                            "upload, one persistent batch launch and a download, uploads overlapping decodes"},
             "ber_6db": ber6, "n_sm": torch.cuda.get_device_properties(dev).multi_processor_count}
 
 
@@ -754,6 +711,107 @@ def run_precision(args):
             "roofline_peaks_tops": {"int": peak_int / 1e12, "fp32": peak_f32 / 1e12}, "points": points}
 
 
+def run_tc(args):
+    """The tensor-core radix-4 variant (vd_decode_tc, the paper's D = Theta_hat L
+    + Lambda with dragonfly groups, Sec. VIII) on the bench workload: one
+    launch per 2^24-bit stream, six per step, against the CUDA-core batch
+    decode of the same streams (identical bits).  Roofline as the bench line
+    (255 ACS ops per decoded bit against the integer-issue peak), plus the
+    tensor operations it issues: 2 mma m16n8k16 per stage pair and frame."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+    dev = torch.device("cuda", 0)
+    code = vd.Code(K, synth.K7_GENS)
+    streams = [synth.segmented_stream(e).s8().view(np.uint8) for e in EBN0S]
+    nw = N_INFO // 32
+    arena = torch.from_numpy(np.concatenate(streams)).to(dev)
+    llr = [arena[i * BETA * N_INFO:(i + 1) * BETA * N_INFO] for i in range(len(streams))]
+    out = torch.empty(nw * len(streams), dtype=torch.int32, device=dev)
+    outs = [out[i * nw:(i + 1) * nw] for i in range(len(streams))]
+    s = torch.cuda.Stream(dev)
+
+    def step():
+        for i in range(len(streams)):
+            vd.vd_decode_tc(code.handle, llr[i], N_INFO, F, V, 0, outs[i], stream=s)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 20))
+    a.record(s)
+    for _ in range(reps):
+        step()
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    vd.vd_sync(s)
+    ms = a.elapsed_time(b) / reps
+    ref = torch.empty_like(out)
+    plan = stream_plan(vd, code, len(streams), 2, 1, s)
+    plan.launch(arena, ref, stream=s)
+    torch.cuda.synchronize(dev)
+    plan.close()
+    bits = N_INFO * len(streams)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * 128 * 2 * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    frames = len(streams) * (N_INFO // F)
+    return {"workload": "6 streams x 2^24 info bits, K=7 r1/2, f=256, v=42, int8 LLR; one vd_decode_tc per stream",
+            "gbps": bits / (ms / 1e3) / 1e9, "ms_per_step": ms, "identical_to_cuda_core": bool(torch.equal(out, ref)),
+            "roofline_frac_integer_peak": bits / (ms / 1e3) * ops_per_bit() / peak,
+            "mma_m16n8k16_per_step": frames * ((F + 2 * V) // 2) * 2,
+            "form": "one warp per frame; 2 mma.sync.m16n8k16 f16->f32 per stage pair; 4-way max by shuffles"}
+
+
+def run_radix(args):
+    """The general radix-2^rho variant (vd_decode_radix, Sec. VI / Eq.
+    general:S) for rho = 1, 2, 3 on the bench workload (one launch per 2^24-bit
+    stream), each checked bit for bit against the CUDA-core batch decode."""
+    import torch
+    import paper_2011_13579_gb300 as vd
+    from paper_2011_13579_gb300 import synth
+    dev = torch.device("cuda", 0)
+    code = vd.Code(K, synth.K7_GENS)
+    streams = [synth.segmented_stream(e).s8().view(np.uint8) for e in EBN0S]
+    nw = N_INFO // 32
+    arena = torch.from_numpy(np.concatenate(streams)).to(dev)
+    llr = [arena[i * BETA * N_INFO:(i + 1) * BETA * N_INFO] for i in range(len(streams))]
+    s = torch.cuda.Stream(dev)
+    ref = torch.empty(nw * len(streams), dtype=torch.int32, device=dev)
+    plan = stream_plan(vd, code, len(streams), 2, 1, s)
+    plan.launch(arena, ref, stream=s)
+    torch.cuda.synchronize(dev)
+    plan.close()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * 128 * 2 * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    res = {"workload": "6 streams x 2^24 info bits, K=7 r1/2, f=256, v=42, int8 LLR; one vd_decode_radix per stream",
+           "form": "one warp per frame, int32 metrics in shared memory, survivors in global scratch", "rho": {}}
+    bits = N_INFO * len(streams)
+    for rho in (1, 2, 3):
+        out = torch.empty_like(ref)
+        outs = [out[i * nw:(i + 1) * nw] for i in range(len(streams))]
+
+        def step():
+            for i in range(len(streams)):
+                vd.vd_decode_radix(code.handle, llr[i], N_INFO, F, V, rho, 0, outs[i], stream=s)
+
+        step()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record(s)
+        for _ in range(reps):
+            step()
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        vd.vd_sync(s)
+        ms = a.elapsed_time(b) / reps
+        res["rho"][str(rho)] = {"gbps": bits / (ms / 1e3) / 1e9, "ms_per_step": ms,
+                                "identical_to_cuda_core": bool(torch.equal(out, ref)),
+                                "roofline_frac_integer_peak": bits / (ms / 1e3) * ops_per_bit() / peak}
+    return res
+
+
 def packets_only(args):
     """The uneven-packet plan (65,536 packets by default) with a fixed kernel
     shape (radix 2, one lane: no autotuning launches), W + K CUDA-graph
@@ -832,7 +890,8 @@ def main():
     ap.add_argument("--serving-pool", type=int, default=8192)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-max-packets", type=int, default=400000)
-    ap.add_argument("--workload", default="stream", choices=["stream", "precision", "packets", "intpeak"],
+    ap.add_argument("--workload", default="stream",
+                    choices=["stream", "precision", "packets", "intpeak", "tc", "radix"],
                     help="precision: the K=9 precision study (int8 / 4-bit / fp16) instead of the bench line; "
                          "packets: only W+K graph launches of the uneven-packet plan (for profilers); "
                          "intpeak: only the integer-issue microbenchmark")
@@ -840,8 +899,6 @@ def main():
     ap.add_argument("--precision-bits", type=int, default=1 << 24)
     ap.add_argument("--precision-ebn0", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.0, 1.0, 2.0, 3.0, 4.0])
-    ap.add_argument("--e2e-parts", type=int, default=6,
-                    help="end-to-end leg: plans the streams are split into so uploads overlap decoding")
     ap.add_argument("--packets", type=int, default=65536,
                     help="packets of the batched-vs-plain comparison (0: skip it)")
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
@@ -888,6 +945,12 @@ def main():
         return
     if args.workload == "packets":
         packets_only(args)
+        return
+    if args.workload == "radix":
+        print(json.dumps({"radix_variant": run_radix(args)}), flush=True)
+        return
+    if args.workload == "tc":
+        print(json.dumps({"tensor_core_variant": run_tc(args)}), flush=True)
         return
     if args.workload == "intpeak":
         import torch

@@ -148,6 +148,28 @@ vd_status vd_decode(const vd_code *code, const void *d_llr, int llr_type, int64_
                     const vd_tune *tune, void *stream);
 
 /*
+ * vd_decode_host — vd_decode from and to host memory, for n_streams streams
+ * of the same length and configuration: the library uploads each stream's
+ * received values, decodes it (the persistent batch kernel, one stream per
+ * launch on two alternating decode streams) and downloads its packed bits,
+ * so stream i+1 uploads while stream i decodes and stream i's words come
+ * back while later streams decode.  Same frames (Sec. III) and bits as
+ * vd_decode; radix as given, the library's lane count.
+ *   h_llr[i]: stream i's int8 LLRs (unpunctured), (n_info (+K-1)) x beta
+ *             bytes; page-locked memory for the copies to overlap (pageable
+ *             works, without overlap).
+ *   h_out[i]: ceil(n_info/32) words (written when `stream` completes).
+ * The device copies and the two plans live in library memory kept for this
+ * stream (allocated on the first call and when the configuration changes).
+ * Asynchronous: the caller waits on `stream`.  A call starts after earlier
+ * work on `stream`, so consecutive calls on one stream do not overlap.
+ * VD_EINVAL / VD_EUNSUPPORTED / VD_ENOMEM / VD_ECUDA as vd_decode.
+ */
+vd_status vd_decode_host(const vd_code *code, int n_streams, const void *const *h_llr, int llr_type,
+                         int64_t n_info, int f, int v, int radix, uint32_t flags, uint32_t *const *h_out,
+                         void *stream);
+
+/*
  * The configuration vd_decode uses for this code and LLR type when its tune
  * argument is NULL: f, v and radix as given, and the lanes per frame pair and
  * threads per block it picks.  The decoded bits depend only on f, v and the
@@ -244,6 +266,36 @@ vd_status vd_decode_each(const vd_code *const *codes, int n_codes, const vd_pack
                          int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena, int radix,
                          void *const *streams, int n_streams);
 
+/*
+ * vd_decode_tc — the paper's tensor-core formulation of the radix-4 forward
+ * procedure (Sec. VIII: D = Theta_hat L + Lambda per stage pair, the
+ * dragonfly groups of Sec. VIII-D-2 so that four Theta_hat in one A operand
+ * serve all 16 dragonflies), as a measured variant of vd_decode.  Two
+ * mma.sync.m16n8k16 (f16 x f16 -> f32, exact for int8 LLRs) per stage pair
+ * and frame, one warp per frame; same frames, tie rules and bits as
+ * vd_decode.  Arguments as vd_decode for unpunctured int8 LLRs of K=7,
+ * beta=2 codes whose dragonflies form at most four groups (the (2,1,7)
+ * 171/133 code); frames of at most 1024 stages (f + 2 v).
+ * VD_EUNSUPPORTED otherwise.  Asynchronous on stream.
+ */
+vd_status vd_decode_tc(const vd_code *code, const void *d_llr, int64_t n_info, int f, int v, uint32_t flags,
+                       uint32_t *d_out, void *stream);
+
+/*
+ * vd_decode_radix — the general radix-2^rho forward procedure of Sec. VI as a
+ * measured variant of vd_decode: rho = 1, 2 or 3 trellis stages per step
+ * (radix 2, 4, 8), the states of each group of 2^rho left and right states
+ * indexed by Eq. general:S, every right state taking the best of its 2^rho
+ * candidates (rho branch metrics each) with a rho-bit survivor; one warp per
+ * frame, metrics in shared memory, survivors in the library's scratch pool
+ * (allocated on first use).  Same frames, tie rules and bits as vd_decode.
+ * Arguments as vd_decode for unpunctured int8 LLRs of the K=7 and K=9 codes.
+ * VD_EINVAL on bad arguments (rho outside 1..3), VD_EUNSUPPORTED otherwise.
+ * Asynchronous on stream.
+ */
+vd_status vd_decode_radix(const vd_code *code, const void *d_llr, int64_t n_info, int f, int v, int rho,
+                          uint32_t flags, uint32_t *d_out, void *stream);
+
 /* One-shot batch decode: plan, launch, wait for `stream`, free. */
 vd_status vd_decode_batch(const vd_code *const *codes, int n_codes, const vd_packet *packets,
                           int64_t n_packets, const void *d_llr_arena, uint32_t *d_out_arena,
@@ -295,11 +347,21 @@ typedef struct vd_server_stats {
 vd_status vd_server_create(vd_server **out, const vd_code *const *codes, int n_codes,
                            const vd_server_config *cfg);
 
-/* Queues one packet: n_values received values (int8, or 4-bit two per byte) in
- * host memory, copied before returning; n_info information bits; flags as
- * vd_decode.  Never blocks on the device. */
+/* Queues one packet: n_values received values (int8, 4-bit two per byte, or
+ * hard decisions eight per byte) in host memory, copied before returning into
+ * the server's pinned staging area (from where its batch uploads it into the
+ * device arena; the kernels read device memory only); n_info information
+ * bits; flags as vd_decode.  Never blocks on the device. */
 vd_status vd_server_submit(vd_server *server, int code_id, int llr_type, const void *host_llr,
                            int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag);
+
+/* Queues n host packets in one call (one staging lock and one queue lock):
+ * packet i as vd_server_submit(code_id[i], llr_type[i], host_llr +
+ * llr_offset[i] bytes, n_values[i], n_info[i], flags[i], tags[i]).  Every
+ * packet is checked first; on an error nothing is queued. */
+vd_status vd_server_submit_many(vd_server *server, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                                const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                                const int64_t *n_info, const uint32_t *flags, const uint64_t *tags);
 
 /* As vd_server_submit, for values already in device memory (an upstream
  * stage on the GPU produced them): nothing is copied; the kernels read the
@@ -325,13 +387,16 @@ void vd_server_destroy(vd_server *server);
  * vd_server_replay — open-loop trace replay against a server (a load
  * generator for latency measurement; the paper has no counterpart).
  *
- * Submits packet i (tag i) when arrival_ns[i] nanoseconds (nondecreasing)
+ * Submits packet i (tag i) once arrival_ns[i] nanoseconds (nondecreasing)
  * have passed since the call started — for host packets with n >= 4096
- * from 4 submitting threads, packet i from thread i mod 4 — while the
- * calling thread collects completions, until all n packets have completed.  Packet i: code_id[i], llr_type[i],
- * n_values[i] values at host_llr + llr_offset[i] bytes, n_info[i], flags[i].
- * Outputs: latency_ns[i] = completion time - submit time (host steady clock,
- * -1 if unfinished); if words is not NULL, packet i's decoded words at
+ * from 4 submitting threads, packet i from thread i mod 4, each thread
+ * submitting every packet of its share that has arrived in one
+ * vd_server_submit_many call — while the calling thread collects
+ * completions, until all n packets have completed.  Packet i: code_id[i],
+ * llr_type[i], n_values[i] values at host_llr + llr_offset[i] bytes,
+ * n_info[i], flags[i].  Outputs: latency_ns[i] = completion time - the
+ * packet's scheduled arrival time (host steady clock, so any submit delay
+ * counts; -1 if unfinished); if words is not NULL, packet i's decoded words at
  * words + word_offset[i]; *span_ns (if not NULL) = last completion - first
  * submit.  The server must be idle (nothing submitted and unpolled).
  * Errors: VD_EINVAL (bad arguments, busy server), a submit error,

@@ -25,7 +25,7 @@ __all__ = [
     "vd_batch_plan_info", "vd_batch_plan_packet_tune", "vd_batch_plan_status", "vd_batch_plan_destroy",
     "VdPacket", "VdBatchInfo", "BatchPlan", "VdServerConfig", "VdCompletion", "VdServerStats",
     "Server", "vd_server_create", "vd_server_submit", "vd_server_poll", "vd_server_stats_get",
-    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_bm_gate", "vd_decode_each", "vd_int_peak", "vd_transmit", "vd_transmit_bytes", "transmit", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
+    "vd_server_destroy", "vd_server_replay", "vd_server_submit_device", "vd_server_submit_many", "vd_bm_gate", "vd_decode_each", "vd_decode_tc", "vd_decode_host", "vd_decode_radix", "vd_int_peak", "vd_transmit", "vd_transmit_bytes", "transmit", "vd_get_tune", "vd_decode_noalloc", "vd_noalloc_scratch_limit", "vd_sync", "vd_num_frames", "vd_num_kept", "vd_scratch_bytes", "vd_release_scratch",
     "vd_last_error", "vd_version", "Code", "decode",
 ]
 
@@ -155,10 +155,19 @@ def lib():
         L.vd_server_replay_device.restype = i32
         L.vd_server_submit_device.argtypes = [vp, i32, i32, vp, i64, i64, u32, ctypes.c_uint64]
         L.vd_server_submit_device.restype = i32
+        L.vd_server_submit_many.argtypes = [vp, i64, P(ctypes.c_int32), P(ctypes.c_int32), vp, P(i64), P(i64),
+                                            P(i64), P(u32), P(ctypes.c_uint64)]
+        L.vd_server_submit_many.restype = i32
         L.vd_get_tune.argtypes = [vp, i32, i32, i32, i32, P(VdTune)]
         L.vd_get_tune.restype = i32
         L.vd_bm_gate.argtypes = [i32, vp, i64, i32, vp, vp, vp]
         L.vd_bm_gate.restype = i32
+        L.vd_decode_host.argtypes = [vp, i32, P(vp), i32, i64, i32, i32, i32, u32, P(vp), vp]
+        L.vd_decode_host.restype = i32
+        L.vd_decode_radix.argtypes = [vp, vp, i64, i32, i32, i32, u32, vp, vp]
+        L.vd_decode_radix.restype = i32
+        L.vd_decode_tc.argtypes = [vp, vp, i64, i32, i32, u32, vp, vp]
+        L.vd_decode_tc.restype = i32
         L.vd_decode_each.argtypes = [P(vp), i32, P(VdPacket), i64, vp, vp, i32, P(vp), i32]
         L.vd_decode_each.restype = i32
         L.vd_int_peak.argtypes = [i32, i64, i32, vp, vp, vp]
@@ -250,6 +259,32 @@ def vd_bm_gate(variant, llr_words, n_pairs, n_stages, checksum, metrics=None, st
                             ctypes.c_void_p(checksum.data_ptr()),
                             ctypes.c_void_p(metrics.data_ptr()) if metrics is not None else None,
                             _stream_handle(stream)))
+
+
+def vd_decode_host(handle, host_llrs, n_info, f, v, radix, flags, host_outs, stream=None,
+                   llr_type=VD_LLR_S8) -> None:
+    """vd_decode from host buffers: ``host_llrs`` / ``host_outs`` are lists of
+    (preferably pinned) CPU tensors or numpy arrays, one per stream."""
+    def ptr(x):
+        return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    n = len(host_llrs)
+    ins = (ctypes.c_void_p * n)(*[ptr(x) for x in host_llrs])
+    outs = (ctypes.c_void_p * n)(*[ptr(x) for x in host_outs])
+    _check(lib().vd_decode_host(ctypes.c_void_p(handle), n, ins, int(llr_type), int(n_info), int(f), int(v),
+                                int(radix), int(flags), outs, _stream_handle(stream)))
+
+
+def vd_decode_radix(handle, llr, n_info, f, v, rho, flags, out, stream=None) -> None:
+    """The general radix-2^rho (Sec. VI) variant on device tensors."""
+    _check(lib().vd_decode_radix(ctypes.c_void_p(handle), ctypes.c_void_p(llr.data_ptr()), int(n_info), int(f),
+                                 int(v), int(rho), int(flags), ctypes.c_void_p(out.data_ptr()),
+                                 _stream_handle(stream)))
+
+
+def vd_decode_tc(handle, llr, n_info, f, v, flags, out, stream=None) -> None:
+    """The tensor-core (Sec. VIII) radix-4 variant on device tensors."""
+    _check(lib().vd_decode_tc(ctypes.c_void_p(handle), ctypes.c_void_p(llr.data_ptr()), int(n_info), int(f),
+                              int(v), int(flags), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
 
 def vd_decode_each(codes, packets, llr_arena, out_arena, radix, streams) -> None:
@@ -490,6 +525,23 @@ def vd_server_destroy(server) -> None:
         lib().vd_server_destroy(ctypes.c_void_p(server))
 
 
+def vd_server_submit_many(server, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, tags):
+    """host_llr: a contiguous numpy array; the other arguments numpy arrays of
+    one entry per packet (offsets in bytes)."""
+    import numpy as np
+    P = ctypes.POINTER
+    arrs = [np.ascontiguousarray(code_id, np.int32), np.ascontiguousarray(llr_type, np.int32),
+            np.ascontiguousarray(llr_offset, np.int64), np.ascontiguousarray(n_values, np.int64),
+            np.ascontiguousarray(n_info, np.int64), np.ascontiguousarray(flags, np.uint32),
+            np.ascontiguousarray(tags, np.uint64)]
+    types = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
+             ctypes.c_uint64]
+    ptrs = [a.ctypes.data_as(P(t)) for a, t in zip(arrs, types)]
+    _check(lib().vd_server_submit_many(ctypes.c_void_p(server), len(arrs[0]), ptrs[0], ptrs[1],
+                                       ctypes.c_void_p(host_llr.ctypes.data), ptrs[2], ptrs[3], ptrs[4], ptrs[5],
+                                       ptrs[6]))
+
+
 def vd_server_submit_device(server, code_id, llr_type, d_llr, n_values, n_info, flags, tag):
     """d_llr: a contiguous CUDA tensor (or a device address) holding the packet's values."""
     addr = d_llr if isinstance(d_llr, int) else d_llr.data_ptr()
@@ -564,6 +616,9 @@ class Server:
 
     def submit_device(self, code_id, llr_type, d_llr, n_values, n_info, flags, tag):
         vd_server_submit_device(self.handle, code_id, llr_type, d_llr, n_values, n_info, flags, tag)
+
+    def submit_many(self, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, tags):
+        vd_server_submit_many(self.handle, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, tags)
 
     def close(self):
         h, self.handle = getattr(self, "handle", None), None

@@ -11,6 +11,7 @@
 #include <string>
 #include <tuple>
 #include <utility>
+#include <vector>
 
 #include "../../include/vd.h"
 #include "vd_code.h"
@@ -140,7 +141,9 @@ struct Scratch {
 
 std::mutex g_scratch_mu;
 // (device, stream, slot) -> buffer; slot 0 = survivors, 1 = depunctured LLRs,
-// 2 = the status word (stream 0), 3 = the persistent kernel's task counter
+// 2 = the status word (stream 0), 3 = the persistent kernel's task counter,
+// 4 / 5 = vd_decode_host's device copies of the LLRs / decoded words,
+// 6 = vd_decode_radix's survivors
 std::map<std::tuple<int, uintptr_t, int>, Scratch> g_scratch;
 
 vd_status get_scratch(int slot, size_t bytes, cudaStream_t st, void **out) {
@@ -532,6 +535,138 @@ extern "C" vd_status vd_decode_each(const vd_code *const *codes, int n_codes, co
     return VD_OK;
 }
 
+// ------------------------------------------------ decode from host memory
+
+namespace {
+
+constexpr int kHostComp = 2;   // decode streams of vd_decode_host
+
+// Copy and decode streams, events and the two single-stream batch plans of
+// vd_decode_host, per (device, caller stream), rebuilt when the stream
+// configuration changes.
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr, comp[kHostComp] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;
+    vd_batch_plan *plan[kHostComp] = {nullptr, nullptr};
+    const vd_code *code = nullptr;
+    int64_t n_info = -1;
+    int f = 0, v = 0, radix = 0;
+    uint32_t flags = 0;
+};
+std::mutex g_pipe_mu;
+std::map<std::pair<int, uintptr_t>, HostPipe> g_pipes;
+
+vd_status host_pipe(const vd_code *c, int64_t n_info, int f, int v, int radix, uint32_t flags, cudaStream_t cs,
+                    size_t n_events, HostPipe **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    HostPipe &hp = g_pipes[std::make_pair(dev, (uintptr_t)cs)];
+    if (!hp.in) {
+        if ((e = cudaStreamCreateWithFlags(&hp.in, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&hp.out, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&hp.comp[0], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&hp.comp[1], cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate (host pipeline)");
+    }
+    while (hp.ev.size() < n_events) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate (host pipeline)");
+        hp.ev.push_back(ev);
+    }
+    if (hp.code != c || hp.n_info != n_info || hp.f != f || hp.v != v || hp.radix != radix || hp.flags != flags) {
+        for (auto &pl : hp.plan) {
+            if (pl) {
+                cudaDeviceSynchronize();
+                vd_batch_plan_destroy(pl);
+                pl = nullptr;
+            }
+        }
+        // one packet: a whole stream at offset 0 of the arenas given at launch
+        vd_packet pk;
+        memset(&pk, 0, sizeof pk);
+        pk.code_id = 0;
+        pk.llr_type = VD_LLR_S8;
+        pk.n_info = n_info;
+        pk.flags = flags;
+        pk.f = f;
+        pk.v = v;
+        vd_tune tune;
+        memset(&tune, 0, sizeof tune);
+        tune.radix = radix;
+        if (!default_lanes(c->kind, &tune.lanes)) return fail(VD_EUNSUPPORTED, "no kernel for this code");
+        const vd_code *codes[1] = {c};
+        for (int k = 0; k < kHostComp; ++k) {
+            const vd_status st = vd_batch_plan_create(&hp.plan[k], codes, 1, &pk, 1, &tune, hp.comp[k]);
+            if (st != VD_OK) return st;
+        }
+        hp.code = c;
+        hp.n_info = n_info;
+        hp.f = f;
+        hp.v = v;
+        hp.radix = radix;
+        hp.flags = flags;
+    }
+    *out = &hp;
+    return VD_OK;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_decode_host(const vd_code *c, int n_streams, const void *const *h_llr, int llr_type,
+                                    int64_t n_info, int f, int v, int radix, uint32_t flags,
+                                    uint32_t *const *h_out, void *stream) {
+    if (n_streams < 1 || !h_llr || !h_out) return fail(VD_EINVAL, "vd_decode_host: bad stream arrays");
+    for (int i = 0; i < n_streams; ++i)
+        if (!h_llr[i] || !h_out[i]) return fail(VD_EINVAL, "vd_decode_host: NULL host buffer %d", i);
+    vd_status st = check_decode_args(c, h_llr[0], llr_type, n_info, f, v, radix, flags, h_out[0]);
+    if (st != VD_OK) return st;
+    if (llr_type != VD_LLR_S8 || c->punctured)
+        return fail(VD_EUNSUPPORTED, "vd_decode_host: unpunctured int8 LLRs only");
+    if (n_info == 0) return VD_OK;
+    const cudaStream_t cs = (cudaStream_t)stream;
+    const int64_t T = n_info + ((flags & VD_TERMINATED) ? c->K - 1 : 0);
+    const size_t llr_bytes = (size_t)T * c->beta, llr_stride = (llr_bytes + 255) & ~(size_t)255;
+    const int64_t n_words = (n_info + 31) / 32;
+    const size_t out_stride = ((size_t)n_words * 4 + 255) & ~(size_t)255;
+
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    HostPipe *hp = nullptr;
+    st = host_pipe(c, n_info, f, v, radix, flags, cs, 2 * (size_t)n_streams + 2, &hp);
+    if (st != VD_OK) return st;
+    void *d_llr = nullptr, *d_out = nullptr;
+    if ((st = get_scratch(4, llr_stride * n_streams, cs, &d_llr)) != VD_OK) return st;
+    if ((st = get_scratch(5, out_stride * n_streams, cs, &d_out)) != VD_OK) return st;
+    cudaError_t e;
+    // everything below starts after earlier work on the caller's stream (which
+    // may still read the device copies)
+    size_t evi = 0;
+    cudaEvent_t entry = hp->ev[evi++];
+    if ((e = cudaEventRecord(entry, cs)) != cudaSuccess) return cuda_fail(e, "vd_decode_host: ordering");
+    for (cudaStream_t x : {hp->in, hp->out, hp->comp[0], hp->comp[1]})
+        if ((e = cudaStreamWaitEvent(x, entry, 0)) != cudaSuccess) return cuda_fail(e, "vd_decode_host: ordering");
+    // stream i: upload (copy stream), decode (decode stream i mod 2) once its
+    // bytes are on the device, download its words (download stream)
+    for (int i = 0; i < n_streams; ++i) {
+        uint8_t *dllr = (uint8_t *)d_llr + llr_stride * i;
+        uint32_t *dout = (uint32_t *)((uint8_t *)d_out + out_stride * i);
+        const int k = i % kHostComp;
+        cudaEvent_t up = hp->ev[evi++], dec = hp->ev[evi++];
+        if ((e = cudaMemcpyAsync(dllr, h_llr[i], llr_bytes, cudaMemcpyHostToDevice, hp->in)) != cudaSuccess ||
+            (e = cudaEventRecord(up, hp->in)) != cudaSuccess || (e = cudaStreamWaitEvent(hp->comp[k], up, 0)) != cudaSuccess)
+            return cuda_fail(e, "vd_decode_host: upload");
+        if ((st = vd_batch_plan_launch(hp->plan[k], dllr, dout, hp->comp[k])) != VD_OK) return st;
+        if ((e = cudaEventRecord(dec, hp->comp[k])) != cudaSuccess || (e = cudaStreamWaitEvent(hp->out, dec, 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h_out[i], dout, (size_t)n_words * 4, cudaMemcpyDeviceToHost, hp->out)) != cudaSuccess)
+            return cuda_fail(e, "vd_decode_host: download");
+    }
+    cudaEvent_t done = hp->ev[evi++];
+    if ((e = cudaEventRecord(done, hp->out)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, done, 0)) != cudaSuccess)
+        return cuda_fail(e, "vd_decode_host: ordering");
+    return VD_OK;
+}
+
 extern "C" vd_status vd_get_tune(const vd_code *c, int llr_type, int f, int v, int radix, vd_tune *out) {
     if (!c || !out) return fail(VD_EINVAL, "NULL argument");
     if (f <= 0 || v < 0) return fail(VD_EINVAL, "f must be positive and v >= 0");
@@ -549,6 +684,15 @@ extern "C" vd_status vd_get_tune(const vd_code *c, int llr_type, int f, int v, i
     out->lanes = lanes;
     out->threads = vd::kThreads;
     return VD_OK;
+}
+
+vd_status vd_internal_scratch(int slot, size_t bytes, cudaStream_t stream, void **out) {
+    return get_scratch(slot, bytes, stream, out);
+}
+
+int *vd_internal_status_word(void) {
+    int *w = nullptr;
+    return device_status_word(nullptr, &w) == VD_OK ? w : nullptr;
 }
 
 extern "C" const char *vd_last_error(void) { return g_err.c_str(); }

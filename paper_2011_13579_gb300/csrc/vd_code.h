@@ -24,6 +24,14 @@ void vd_internal_set_error(const char *msg);
 // device (VD_EBOUNDS if a kernel set it); called by vd_sync.
 vd_status vd_internal_noalloc_status(void);
 
+// The library's device status word of the current device (created on first
+// use; NULL if it cannot be allocated), for kernels outside vd_api.cu.
+int *vd_internal_status_word(void);
+
+// A buffer of at least `bytes` from the library's scratch pool of the current
+// device and `stream` (slots 0-5 belong to vd_api.cu; 6 = vd_decode_radix).
+vd_status vd_internal_scratch(int slot, size_t bytes, cudaStream_t stream, void **out);
+
 namespace vd {
 
 // Input pre-pass shared by batches and the server: expands the transmitted

@@ -6,8 +6,12 @@
 //
 // Memory: one device arena (LLRs, depunctured LLRs and outputs of admitted
 // packets) with a pinned host mirror at the same offsets.  Each micro-batch
-// takes one contiguous arena region (first fit, freed on completion), so its
-// inputs go down in one copy and its outputs come back in one copy.  Every
+// takes one contiguous arena region (first fit, freed on completion).  Host
+// packets are copied once, at submit, into a pinned staging area; a batch's
+// staged packets keep their staging layout in the region, so each run of
+// packets that are contiguous in staging goes down in one copy (and those
+// that did not fit in staging in one more, from the mirror); the kernels
+// read device memory only.  The outputs come back in one copy.  Every
 // per-stream buffer (descriptors, work list, survivor scratch) is allocated
 // once, when the server is created.
 #include <cuda_runtime.h>
@@ -59,9 +63,8 @@ struct Req {
     int64_t n_info, T;
     uint32_t flags;
     int32_t f, v;
-    std::vector<uint8_t> llr;      // received values as submitted (host packets)
-    const uint8_t *dev_llr;        // values the kernels read in place: the caller's device buffer, or
-                                   // the packet's copy in the pinned staging area (mapped)
+    std::vector<uint8_t> llr;      // received values as submitted (host packets that did not fit in staging)
+    const uint8_t *dev_llr;        // device packets: the caller's buffer, read in place; else NULL
     size_t stage_off, stage_bytes; // the packet's staging region (stage_bytes 0: none)
     size_t in_bytes, prep_bytes, out_words;
     int64_t submit_ns, admit_ns, done_ns;
@@ -127,6 +130,9 @@ struct Slot {
     bool busy = false;
     std::vector<Req *> reqs;
     size_t region_off = 0, region_bytes = 0;
+    struct Run { size_t stage_off, region_off, bytes; };
+    std::vector<Run> runs;         // staged inputs: one copy per run contiguous in staging
+    size_t mirror_lo = 0, mirror_hi = 0;   // region bytes of the inputs that come from the mirror
     KindRes kinds[kMaxKinds];
     vd::PrepJob *d_jobs = nullptr;
     int *d_counters = nullptr;
@@ -144,10 +150,9 @@ struct vd_server {
     int device = 0, n_sm = 0;
     uint8_t *d_arena = nullptr, *h_arena = nullptr;
     Arena arena;
-    // pinned, device-mapped staging for host packets: submit copies the
-    // values there once and the kernels read them over the host link, so
-    // the worker neither copies them again nor uploads them
-    uint8_t *h_stage = nullptr, *d_stage = nullptr;
+    // pinned staging for host packets: submit copies the values there once,
+    // and each batch uploads its staged packets from there in a few copies
+    uint8_t *h_stage = nullptr;
     Arena stage;
     std::mutex stage_mu;
     std::vector<Slot> slots;
@@ -209,10 +214,15 @@ bool launch_batch(vd_server *s, Slot &sl) {
     const cudaStream_t st = sl.st;
     uint8_t *dbase = s->d_arena + sl.region_off;
     uint8_t *hbase = s->h_arena + sl.region_off;
-    // inputs: one copy of the region's input part (laid out first)
-    size_t in_end = 0;
-    for (Req *r : sl.reqs) in_end = std::max(in_end, r->in_off + r->in_bytes);
-    if (in_end && cudaMemcpyAsync(dbase, hbase, in_end, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
+    // inputs: one copy per run of staged packets, one of the rest from the mirror
+    for (const Slot::Run &run : sl.runs)
+        if (cudaMemcpyAsync(dbase + run.region_off, s->h_stage + run.stage_off, run.bytes, cudaMemcpyHostToDevice,
+                            st) != cudaSuccess)
+            return false;
+    if (sl.mirror_hi > sl.mirror_lo &&
+        cudaMemcpyAsync(dbase + sl.mirror_lo, hbase + sl.mirror_lo, sl.mirror_hi - sl.mirror_lo,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return false;
     // pre-pass for punctured / 4-bit packets
     int64_t n_jobs = 0;
     for (Req *r : sl.reqs) {
@@ -390,14 +400,33 @@ void worker_main(vd_server *s) {
             }
             if (!batch.empty()) {
                 {
-                    // lay out: inputs, then pre-pass outputs, then decoded words
+                    // lay out: staged inputs (runs contiguous in staging keep their
+                    // layout), the other host inputs, pre-pass outputs, decoded words
                     size_t cur = 0;
                     const int64_t t = now_ns();
-                    for (Req *r : batch) { r->in_off = cur; cur += align_up(r->in_bytes); r->admit_ns = t; }
+                    std::vector<Slot::Run> &runs = free_slot->runs;
+                    runs.clear();
+                    for (Req *r : batch) {
+                        r->admit_ns = t;
+                        if (!r->stage_bytes) continue;
+                        if (!runs.empty() && runs.back().stage_off + runs.back().bytes == r->stage_off) {
+                            r->in_off = runs.back().region_off + runs.back().bytes;
+                            runs.back().bytes += r->stage_bytes;
+                        } else {
+                            r->in_off = cur;
+                            runs.push_back({r->stage_off, cur, r->stage_bytes});
+                        }
+                        cur = r->in_off + r->stage_bytes;
+                    }
+                    free_slot->mirror_lo = cur;
+                    for (Req *r : batch)
+                        if (!r->stage_bytes && r->in_bytes) { r->in_off = cur; cur += align_up(r->in_bytes); }
+                    free_slot->mirror_hi = cur;
                     for (Req *r : batch) { r->prep_off = cur; cur += align_up(r->prep_bytes); }
                     for (Req *r : batch) { r->out_off = cur; cur += align_up(r->out_words * 4); }
                     for (Req *r : batch)
-                        if (r->in_bytes) memcpy(s->h_arena + off + r->in_off, r->llr.data(), r->in_bytes);
+                        if (!r->stage_bytes && r->in_bytes)
+                            memcpy(s->h_arena + off + r->in_off, r->llr.data(), r->in_bytes);
                     free_slot->reqs = batch;
                     free_slot->region_off = off;
                     free_slot->region_bytes = region;
@@ -462,13 +491,12 @@ extern "C" vd_status vd_server_create(vd_server **out, const vd_code *const *cod
     cudaMemset(s->d_status, 0, 256);
     s->arena.init((size_t)c.device_bytes);
     // the staging area is optional: without it host packets go through the arena
-    if (cudaHostAlloc((void **)&s->h_stage, (size_t)c.device_bytes, cudaHostAllocMapped) == cudaSuccess &&
-        cudaHostGetDevicePointer((void **)&s->d_stage, s->h_stage, 0) == cudaSuccess) {
+    if (cudaHostAlloc((void **)&s->h_stage, (size_t)c.device_bytes, cudaHostAllocDefault) == cudaSuccess) {
         s->stage.init((size_t)c.device_bytes);
     } else {
         cudaGetLastError();
         cudaFreeHost(s->h_stage);
-        s->h_stage = s->d_stage = nullptr;
+        s->h_stage = nullptr;
     }
 
     // which kinds are present, with their frame shape
@@ -523,8 +551,9 @@ extern "C" vd_status vd_server_create(vd_server **out, const vd_code *const *cod
 
 namespace {
 
-vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr, bool device,
-                        int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
+// Checks one packet and builds its request (nothing staged or queued yet).
+vd_status make_req(vd_server *s, int code_id, int llr_type, const void *llr, bool device, int64_t n_values,
+                   int64_t n_info, uint32_t flags, uint64_t tag, Req **out, size_t *value_bytes_out) {
     if (!s) return fail(VD_EINVAL, "server is NULL");
     if (code_id < 0 || code_id >= (int)s->codes.size()) return fail(VD_EINVAL, "bad code_id");
     if (llr_type != VD_LLR_S8 && llr_type != VD_LLR_S4 && llr_type != VD_LLR_HARD)
@@ -554,37 +583,84 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
     r->prep_bytes = (c->punctured || llr_type != VD_LLR_S8) ? (size_t)(T * c->beta) : 0;
     r->out_words = (size_t)((n_info + 31) / 32);
     r->stage_off = r->stage_bytes = 0;
-    if (device) {
-        r->dev_llr = (const uint8_t *)llr;
-        r->in_bytes = 0;   // nothing to upload: read in place on the device
-    } else {
-        size_t off = 0;
-        bool staged = false;
-        if (s->h_stage) {
-            std::lock_guard<std::mutex> lk(s->stage_mu);
-            staged = s->stage.alloc(align_up(value_bytes), &off);
-        }
-        if (staged) {
-            memcpy(s->h_stage + off, llr, value_bytes);
-            r->dev_llr = s->d_stage + off;
-            r->stage_off = off;
-            r->stage_bytes = align_up(value_bytes);
-            r->in_bytes = 0;
-        } else {   // staging full: the values travel with the batch's upload
-            r->dev_llr = nullptr;
-            r->in_bytes = value_bytes;
-            r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + r->in_bytes);
-        }
+    r->dev_llr = device ? (const uint8_t *)llr : nullptr;
+    r->in_bytes = device ? 0 : value_bytes;   // device packets: nothing to upload, read in place
+    const size_t need = align_up(r->in_bytes) + align_up(r->prep_bytes) + align_up(r->out_words * 4);
+    if (need > s->arena.cap) { delete r; return fail(VD_ENOMEM, "packet larger than the device arena"); }
+    *out = r;
+    *value_bytes_out = value_bytes;
+    return VD_OK;
+}
+
+// Copies a host packet's values into staging (the caller holds stage_mu),
+// or, when staging is full, into the request itself.
+void stage_req(vd_server *s, Req *r, const void *llr, size_t value_bytes) {
+    size_t off = 0;
+    if (s->h_stage && s->stage.alloc(align_up(value_bytes), &off)) {
+        memcpy(s->h_stage + off, llr, value_bytes);
+        r->stage_off = off;
+        r->stage_bytes = align_up(value_bytes);
+    } else {   // staging full: the values travel through the arena's mirror
+        r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + value_bytes);
     }
-    r->submit_ns = now_ns();
+}
+
+// Queues built requests (one lock) and wakes the worker.
+void enqueue(vd_server *s, Req *const *rs, int64_t n) {
+    const int64_t t = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        const size_t need = align_up(r->in_bytes) + align_up(r->prep_bytes) + align_up(r->out_words * 4);
-        if (need > s->arena.cap) { delete r; return fail(VD_ENOMEM, "packet larger than the device arena"); }
-        s->pending.push_back(r);
-        s->stats.submitted += 1;
+        for (int64_t i = 0; i < n; ++i) {
+            rs[i]->submit_ns = t;
+            s->pending.push_back(rs[i]);
+        }
+        s->stats.submitted += n;
     }
     s->cv.notify_all();
+}
+
+vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr, bool device,
+                        int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
+    Req *r = nullptr;
+    size_t vb = 0;
+    const vd_status st = make_req(s, code_id, llr_type, llr, device, n_values, n_info, flags, tag, &r, &vb);
+    if (st != VD_OK) return st;
+    if (!device) {
+        std::lock_guard<std::mutex> lk(s->stage_mu);
+        stage_req(s, r, llr, vb);
+    }
+    enqueue(s, &r, 1);
+    return VD_OK;
+}
+
+// n packets (values at llr + llr_offset[i] bytes; host memory, or device
+// memory read in place) with one staging lock and one queue lock; packet k
+// is index[k] of the arrays (k without an index).  Checks every packet
+// first: on an error nothing is queued.
+vd_status submit_many(vd_server *s, bool device, int64_t n, const int32_t *code_id, const int32_t *llr_type,
+                      const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
+                      const int64_t *n_info, const uint32_t *flags, const uint64_t *tags, const int64_t *index) {
+    std::vector<Req *> rs((size_t)n, nullptr);
+    std::vector<size_t> vb((size_t)n, 0);
+    const uint8_t *base = (const uint8_t *)host_llr;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t i = index ? index[k] : k;
+        const vd_status st = make_req(s, code_id[i], llr_type[i], base + llr_offset[i], device, n_values[i],
+                                      n_info[i], flags[i], tags ? tags[i] : (uint64_t)i, &rs[(size_t)k],
+                                      &vb[(size_t)k]);
+        if (st != VD_OK) {
+            for (int64_t j = 0; j < k; ++j) delete rs[(size_t)j];
+            return st;
+        }
+    }
+    if (!device) {
+        std::lock_guard<std::mutex> lk(s->stage_mu);
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t i = index ? index[k] : k;
+            stage_req(s, rs[(size_t)k], base + llr_offset[i], vb[(size_t)k]);
+        }
+    }
+    enqueue(s, rs.data(), n);
     return VD_OK;
 }
 
@@ -593,6 +669,19 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
 extern "C" vd_status vd_server_submit(vd_server *s, int code_id, int llr_type, const void *host_llr,
                                       int64_t n_values, int64_t n_info, uint32_t flags, uint64_t tag) {
     return submit_common(s, code_id, llr_type, host_llr, false, n_values, n_info, flags, tag);
+}
+
+extern "C" vd_status vd_server_submit_many(vd_server *s, int64_t n, const int32_t *code_id,
+                                           const int32_t *llr_type, const void *host_llr,
+                                           const int64_t *llr_offset, const int64_t *n_values,
+                                           const int64_t *n_info, const uint32_t *flags, const uint64_t *tags) {
+    if (!s) return fail(VD_EINVAL, "server is NULL");
+    if (n < 0) return fail(VD_EINVAL, "n < 0");
+    if (n == 0) return VD_OK;
+    if (!code_id || !llr_type || !host_llr || !llr_offset || !n_values || !n_info || !flags || !tags)
+        return fail(VD_EINVAL, "a packet array is NULL");
+    return submit_many(s, false, n, code_id, llr_type, host_llr, llr_offset, n_values, n_info, flags, tags,
+                       nullptr);
 }
 
 extern "C" vd_status vd_server_submit_device(vd_server *s, int code_id, int llr_type, const void *d_llr,
@@ -651,6 +740,7 @@ extern "C" void vd_server_destroy(vd_server *s) {
 namespace {
 
 constexpr int kReplayProducers = 4;   // submitting threads of a long replay
+constexpr int kReplayGather = 256;    // packets a producer submits in one call at most
 
 vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_id, const int32_t *llr_type,
                       const void *host_llr, const int64_t *llr_offset, const int64_t *n_values,
@@ -689,8 +779,11 @@ vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_
     std::atomic<int> err{VD_OK};
     std::string err_msg;
     std::mutex err_mu;
+    // Each producer submits, in one call, every packet of its share that has
+    // arrived (up to kReplayGather at a time).
     auto producer = [&](int tid) {
-        for (int64_t i = tid; i < n && !abort.load(std::memory_order_relaxed); i += n_prod) {
+        std::vector<int64_t> due;
+        for (int64_t i = tid; i < n && !abort.load(std::memory_order_relaxed);) {
             for (;;) {
                 const int64_t now = now_ns();
                 const int64_t wait = arrival_ns[i] - (now - t0);
@@ -699,8 +792,14 @@ vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_
                 if (wait > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
                 else std::this_thread::yield();
             }
-            const vd_status st = submit_common(s, code_id[i], llr_type[i], base + llr_offset[i], device,
-                                               n_values[i], n_info[i], flags[i], (uint64_t)i);
+            due.clear();
+            const int64_t now_rel = now_ns() - t0;
+            while (i < n && arrival_ns[i] <= now_rel && (int64_t)due.size() < kReplayGather) {
+                due.push_back(i);
+                i += n_prod;
+            }
+            const vd_status st = submit_many(s, device, (int64_t)due.size(), code_id, llr_type, base, llr_offset,
+                                             n_values, n_info, flags, nullptr, due.data());
             if (st != VD_OK) {
                 std::lock_guard<std::mutex> lk(err_mu);
                 if (err.load() == VD_OK) err_msg = vd_last_error();
@@ -739,7 +838,7 @@ vd_status replay_core(vd_server *s, bool device, int64_t n, const int32_t *code_
                 finish(VD_OK);
                 return fail(VD_ECUDA, "replay: the device reported an error");
             }
-            latency_ns[i] = c.done_ns - c.submit_ns;
+            latency_ns[i] = c.done_ns - (t0 + arrival_ns[i]);   // from the scheduled arrival
             first_submit = std::min(first_submit, c.submit_ns);
             last_done = std::max(last_done, c.done_ns);
             if (words) memcpy(words + word_offset[i], wbuf.data() + c.word_offset, (size_t)c.n_words * 4);

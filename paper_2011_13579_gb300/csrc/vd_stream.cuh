@@ -714,6 +714,7 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     const uint32_t one = threadIdx.y + 1u;
     const uint32_t m1 = 0u - one;
     const uint32_t fwmul = one << FW;   // 2^FW: shifts a record word by one field
+    const uint32_t mul16 = one << 4, mul64 = one << 6;   // 2-bit fields: shifts by two and three fields
     constexpr bool COROLLARY = LV == (1u << BETA) - 1u && MV == (1u << BETA) - 1u;
 
     const int nchunks = Wpad / U;
@@ -879,9 +880,21 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 }
                 if constexpr (KS == ES - 1) {
                     // record word m: register RPW m + i at bits FW i (frame 0)
-                    // and 16 + FW i (frame 1); fields cleared, half by a
-                    // select (ALU) and half by a multiply-add (FMA pipe)
+                    // and 16 + FW i (frame 1).  Two forms, alternating by word
+                    // so that the ALU and FMA pipes stay balanced (measured:
+                    // either form alone is slower):
+                    //  * byte permutes: the low byte of each half holds a
+                    //    register's field (and metric bits above it, which
+                    //    the traceback masks off); prmt(P[a], P[b], 0x6240)
+                    //    puts a's low bytes at bits 0 and 16 and b's at 8 and
+                    //    24, a multiply-add shifts a second such word by one
+                    //    field and a select merges them; the fields are then
+                    //    cleared by selects (ALU);
+                    //  * extracted fields: d = P & FM (ALU), cleared by a
+                    //    multiply-add P - d and gathered by multiply-adds
+                    //    acc = 16 acc + d (FMA pipe).
                     constexpr uint32_t FM = ((1u << ES) - 1u) * 0x00010001u;
+                    auto merge = [](uint32_t a, uint32_t b, uint32_t keep_a) { return (a & keep_a) | (b & ~keep_a); };
                     if constexpr (Cfg::MINNORM && S == U - 1) {
                         // the minimum over the states for the next chunk's
                         // normalisation: min of 8 m + j, fields masked off
@@ -895,15 +908,38 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                     uint32_t rec[NWE];
 #pragma unroll
                     for (int m = 0; m < NWE; ++m) {
-                        uint32_t acc = 0;
+                        const int r0 = RPW * m;
+                        if constexpr (RPW == 4) {
+                            if (m & 1) {
+                                uint32_t acc = 0;
 #pragma unroll
-                        for (int i = RPW - 1; i >= 0; --i) {
-                            const int r = RPW * m + i;
-                            const uint32_t d = P[r] & FM;
-                            P[r] = (i & 1) ? imad(d, m1, P[r]) : (P[r] & ~FM);
-                            acc = (i == RPW - 1) ? d : imad(acc, fwmul, d);
+                                for (int i = RPW - 1; i >= 0; --i) {
+                                    const int r = r0 + i;
+                                    const uint32_t d = P[r] & FM;
+                                    P[r] = imad(d, m1, P[r]);
+                                    acc = (i == RPW - 1) ? d : imad(acc, fwmul, d);
+                                }
+                                rec[m] = acc;
+                            } else {
+                                const uint32_t x = prmt(P[r0], P[r0 + 2], 0x6240u);
+                                const uint32_t y = prmt(P[r0 + 1], P[r0 + 3], 0x6240u);
+                                rec[m] = merge(x, imad(y, fwmul, 0u), 0x07070707u);
+#pragma unroll
+                                for (int i = 0; i < RPW; ++i) P[r0 + i] &= ~FM;
+                            }
+                        } else {
+                            // 2-bit fields: registers r0 + i, r0 + i + 4 shifted by 2 i bits
+                            static_assert(RPW == 8, "2-bit or 4-bit record fields");
+                            const uint32_t x0 = prmt(P[r0], P[r0 + 4], 0x6240u);
+                            const uint32_t x1 = imad(prmt(P[r0 + 1], P[r0 + 5], 0x6240u), fwmul, 0u);
+                            const uint32_t x2 = imad(prmt(P[r0 + 2], P[r0 + 6], 0x6240u), mul16, 0u);
+                            const uint32_t x3 = imad(prmt(P[r0 + 3], P[r0 + 7], 0x6240u), mul64, 0u);
+                            rec[m] = merge(merge(x0, x1, 0x03030303u), merge(x2, x3, 0x30303030u), 0x0F0F0F0Fu);
                         }
-                        rec[m] = acc;
+                        if constexpr (RPW != 4) {
+#pragma unroll
+                            for (int i = 0; i < RPW; ++i) P[r0 + i] &= ~FM;
+                        }
                     }
                     if (tau >= tau_store) store_rec(tau, rec);
                 }

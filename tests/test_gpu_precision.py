@@ -84,3 +84,37 @@ def test_fp16_edges_and_reset(term):
             gb, ob = oracle.unpack_bits(gw, n), oracle.unpack_bits(ow, n)
             bad, _ = check_margin(oc, gb, ob, gap, mx, n, f, v, T)
             assert bad == 0, (K, n, f, v)
+
+
+def test_k9_full_size_fp16_within_tie_margin():
+    """The precision-study configuration at full size: 2^24 K=9 r1/3 bits
+    (f=512, v=64, Eb/N0 = 1 dB) in fp16 with fp32 metrics, every frame within
+    the tie margin of the FP64 oracle on the same fp16 values."""
+    n, f, v = 1 << 24, 512, 64
+    st = synth.precision_stream(1.0, n_info=n)
+    h = st.f16()
+    code = vd.Code(9, synth.K9_GENS)
+    gw = vd.decode(code, torch.from_numpy(h.view(np.uint16)).cuda(), n, f, v,
+                   llr_type=vd.VD_LLR_F16).cpu().numpy().view(np.uint32)
+    vd.vd_sync()
+    oc = oracle.Code(9, synth.K9_GENS)
+    ow, gap, mx = oracle.decode_f64(oc, h.astype(np.float64).reshape(n, 3), n, f, v, threads=THREADS)
+    gb, ob = oracle.unpack_bits(gw, n), oracle.unpack_bits(ow, n)
+    bad, frames = check_margin(oc, gb, ob, gap, mx, n, f, v, n)
+    assert bad == 0, f"{bad} frames disagree with no near-tie ({frames} disagree in all)"
+
+
+def test_k9_full_size_4bit_bit_exact():
+    """The precision-study configuration at full size in 4-bit LLRs: 2^24
+    K=9 r1/3 bits, every decoded bit equal to the int64 oracle's on the same
+    4-bit values."""
+    n, f, v = 1 << 24, 512, 64
+    st = synth.precision_stream(2.0, n_info=n)
+    q4 = st.s4()
+    code = vd.Code(9, synth.K9_GENS)
+    gw = vd.decode(code, torch.from_numpy(synth.pack_s4(q4)).cuda(), n, f, v,
+                   llr_type=vd.VD_LLR_S4).cpu().numpy().view(np.uint32)
+    vd.vd_sync()
+    want = oracle.decode(oracle.Code(9, synth.K9_GENS), q4.reshape(n, 3).astype(np.int32), n, f, v,
+                         threads=THREADS)
+    assert np.array_equal(gw, want)
