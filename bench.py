@@ -448,7 +448,8 @@ def run_serving(args, device_resident=False):
     terminated) is first replayed all at once to measure the server's peak
     packet rate; then for each offered load x the packets arrive as a Poisson
     process of rate x * peak (the aggregate of 256 streams), cycling through
-    the pool.  Latency is host submit to completion seen by the server.
+    the pool.  Latency is from a packet's scheduled arrival time to the
+    server seeing its batch complete (host steady clock).
     device_resident: the pool's values are uploaded once and submitted in
     place (vd_server_submit_device), as from an upstream GPU stage."""
     import torch
@@ -498,7 +499,7 @@ def run_serving(args, device_resident=False):
                         "aggregated) at x * peak",
             "peak_pps": peak_pps, "peak_gbps": pool_bits / (n / peak_pps) / 1e9,
             "points": points, "same_bits_at_every_load": consistent, "batches": int(st.batches),
-            "latency": "host submit -> completion seen by the server (steady clock)"}
+            "latency": "scheduled arrival -> batch completion seen by the server (host steady clock)"}
 
 
 def run_bm_gate(dev, s):

@@ -44,7 +44,7 @@ __device__ __forceinline__ void body(uint32_t (&x)[CH], uint32_t a, uint32_t b, 
         if constexpr (V == 0) {          // 16x2 add
             x[k] = vd::add_u16x2(x[k], a);
         } else if constexpr (V == 1) {   // 16x2 max (of the neighbouring chain: not idempotent)
-            x[k] = vd::max_u16x2(x[k], x[(k + 1) % CH] ^ a);
+            x[k] = vd::max_u16x2(x[k], x[(k + 1) % CH]);
         } else if constexpr (V == 2) {   // fused add-then-max (the butterfly's second half)
             x[k] = vd::addmax_u16x2(x[k], a, b ^ (uint32_t)k);
         } else if constexpr (V == 3) {   // 32-bit multiply-add
@@ -60,7 +60,7 @@ __device__ __forceinline__ void body(uint32_t (&x)[CH], uint32_t a, uint32_t b, 
         } else if constexpr (V == 8) {   // fused add-max and multiply-add, 1:1
             x[k] = (k & 1) ? vd::imad(x[k], m, c) : vd::addmax_u16x2(x[k], a, b ^ (uint32_t)k);
         } else if constexpr (V == 9) {   // 16x2 max and three-input logic, 1:1
-            x[k] = (k & 1) ? lop3_xor3(x[k], a, b) : vd::max_u16x2(x[k], x[(k + 1) % CH] ^ a);
+            x[k] = (k & 1) ? lop3_xor3(x[k], a, b) : vd::max_u16x2(x[k], x[(k + 1) % CH]);
         }
     }
     if constexpr (V == 10) {

@@ -189,3 +189,37 @@ def test_device_resident_packets_match_alone():
         o = int(fl["word_offset"][i])
         assert np.array_equal(words[o:o + got[i].size], got[i]), i
     server.close()
+
+
+def test_submit_many_equals_alone():
+    """Packets queued by one vd_server_submit_many call (host values copied
+    into staging, uploaded into the device arena by the batch) decode to the
+    same bits as each packet decoded alone; a bad packet in the list queues
+    nothing."""
+    codes = make_codes()
+    server = vd.Server(codes)
+    pkts = synth.serving_packets(300, index=9)
+    flat = synth.flatten_packets(pkts)
+    n = len(pkts)
+    types = np.zeros(n, np.int32)
+    flags = np.full(n, vd.VD_TERMINATED, np.uint32)
+    bad_vals = flat["n_values"].copy()
+    bad_vals[7] += 1
+    with pytest.raises(vd.VdError):
+        server.submit_many(flat["code_id"], types, flat["llr"], flat["llr_offset"], bad_vals, flat["n_info"],
+                           flags, np.arange(n, dtype=np.uint64))
+    assert server.stats().submitted == 0
+    server.submit_many(flat["code_id"], types, flat["llr"], flat["llr_offset"], flat["n_values"], flat["n_info"],
+                       flags, np.arange(n, dtype=np.uint64))
+    got = {}
+    t_end = time.time() + 60
+    while len(got) < n and time.time() < t_end:
+        for c, w in server.poll():
+            assert c.status == vd.VD_OK
+            got[c.tag] = w
+        time.sleep(0.001)
+    assert len(got) == n
+    for i, p in enumerate(pkts):
+        want, _, _ = alone(codes, p)
+        assert np.array_equal(got[i], want), i
+    server.close()
