@@ -126,23 +126,25 @@ struct StreamCfg {
     // decision word per stage instead.
     //
     // Min-normalised forms (MINNORM; records of ES = 3 stages, scale 8, or
-    // ES = 2, scale 4): every chunk starts by subtracting the minimum over
-    // the states (folded into its first stage) down to the floor FM = U B,
-    // and a frame that starts from the reset state gets the exact head start
-    // C::HT.  Bounds on m (per half):
-    //   * steady state: after a normalisation m is in [FM, FM + SP] with
+    // ES = 2, scale 4): every branch metric carries + B, so it lies in
+    // [0, 2B] and no metric falls within a chunk (a common per-stage offset
+    // changes no decision, Eq. PM); every chunk starts by subtracting the
+    // minimum over the states (folded into its first stage), which brings
+    // it to the floor FM = 0, and a frame that starts from the reset state
+    // gets the exact head start C::HT.  Bounds on m (per half):
+    //   * steady state: after a normalisation m is in [0, SP] with
     //     SP = (K-1)(delta_max - delta_min) the spread of all metrics once
-    //     every state is reachable; a chunk moves m by at most U B either way,
-    //     so m stays in [0, FM + SP + U B];
+    //     every state is reachable; a chunk adds at most 2 U B, so m stays in
+    //     [0, SP + 2 U B];
     //   * after a head start with t < K-1 stages left in its chunk, states
-    //     not yet reachable from state 0 lie within t B of the old floor and
-    //     the others within t B of it plus HT, so the next normalisation
-    //     leaves m <= FM + HT + 2 t B, and the next chunk adds U B.
+    //     not yet reachable from state 0 lie within 2 t B of the old floor and
+    //     the others within 2 t B of it plus HT, so the next normalisation
+    //     leaves m <= HT + 2 t B, and the next chunk adds 2 U B.
     // The largest 2^ES m + 2^ES - 1 must stay within 16 unsigned bits.
-    static constexpr int FM = U * C::B;
+    static constexpr int FM = 0;
     static constexpr int TMAX = U < NB - 1 ? U : NB - 1;
-    static constexpr int TOPM_STEADY = 2 * NB * C::B + U * C::B;
-    static constexpr int TOPM_RESET = C::HT + (2 * TMAX + U) * C::B;
+    static constexpr int TOPM_STEADY = 2 * NB * C::B + 2 * U * C::B;
+    static constexpr int TOPM_RESET = C::HT + (2 * TMAX + 2 * U) * C::B;
     static constexpr int TOPM = FM + (TOPM_STEADY > TOPM_RESET ? TOPM_STEADY : TOPM_RESET);
     static constexpr bool ES3_OK = !RADIX4 && NB % 3 == 0 && U % 3 == 0 && NR % 4 == 0 &&
                                    8 * TOPM + 7 <= 65535;
@@ -186,7 +188,7 @@ struct StreamCfg {
     // (K-1)B + B after a normalisation, so a floor F >= (3(K-1) + 1) B keeps
     // them >= 0.
     static_assert(MINNORM || ES != 2 || F >= (3 * NB + 1) * C::B, "unclamped normalisation floor");
-    static_assert(!MINNORM || F >= U * C::B, "min-normalisation floor covers a chunk's fall");
+    static_assert(!MINNORM || F == 0, "biased branch metrics: min-normalisation to zero");
 };
 
 template <typename Fn, int... S>
@@ -614,8 +616,8 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
     constexpr uint32_t LV = C::lv(), MV = C::mv();
     constexpr uint32_t F2 = (uint32_t)(Cfg::SC * Cfg::F) * 0x00010001u;
     constexpr uint32_t S2 = (uint32_t)(Cfg::SC * Cfg::HS) * 0x00010001u;   // head start
-    // all-equal start and normalisation target: state 0 at F + S (ES = 0, 2),
-    // or the minimum over the states at the floor F (ES = 3)
+    // all-equal start and normalisation target: state 0 at F + S (state-0
+    // forms), or the minimum over the states at the floor F = 0 (min-normalised)
     constexpr uint32_t SEED0 = (uint32_t)(Cfg::SC * (Cfg::MINNORM ? Cfg::F : Cfg::F + C::S)) * 0x00010001u;
     constexpr int ES = Cfg::ES, RPW = Cfg::RPW, FW = Cfg::FW;
 
@@ -742,15 +744,14 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
         // embedded form: the normalisation at a chunk boundary is folded
         // into the branch metrics of the chunk's first stage (adding tn to
         // every candidate shifts every new metric by tn, as normalising
-        // before the stage would).  Min-normalised forms: tn = 2^ES F -
-        // (minimum over the states, taken at the end of the previous chunk)
-        // every chunk; the state-0 form: tn = 4(F+S) - (metric of state 0)
-        // every NORM_CHUNKS chunks, else 0.
+        // before the stage would).  Min-normalised forms: tn = -(minimum over
+        // the states, taken at the end of the previous chunk) every chunk;
+        // the state-0 form: tn = 4(F+S) - (metric of state 0) every
+        // NORM_CHUNKS chunks, else 0.
         uint32_t tn = 0, tn1 = 0, tn2 = 0;
         if constexpr (Cfg::MINNORM) {
             tn = sub_s16x2(SEED0, pmin);
-            tn1 = add_u16x2(tn, 0x00010001u);   // -x + tn = ~x + tn1
-            tn2 = add_u16x2(tn, 0x00020002u);   // -x + 1 + tn (odd candidates of stage 0)
+            tn2 = add_u16x2(tn, 0x00010001u);   // + the odd candidates' mark of stage 0
         } else if constexpr (EMB) {
             uint32_t ref = P[0];
             if constexpr (L > 1) ref = __shfl_sync(gmask, ref, grp_base);
@@ -822,9 +823,64 @@ __device__ __forceinline__ bool forward_pair(const FrameTask (&ft)[2], uint32_t 
                 // decision arithmetic.
                 constexpr int KS = S % ES;   // stage within the record
                 constexpr uint32_t OFF = 0x00010001u << KS;
-                constexpr uint32_t SCM = (0xFFFFu & ~(uint32_t)(Cfg::SC - 1)) * 0x00010001u;
+                [[maybe_unused]] constexpr uint32_t SCM = (0xFFFFu & ~(uint32_t)(Cfg::SC - 1)) * 0x00010001u;
                 uint32_t A4[1 << BETA], A4o[1 << BETA];
-                if constexpr (COROLLARY) {
+                if constexpr (Cfg::MINNORM) {
+                    // biased pattern sums Ab[x] = A[x] + B in [0, 2B] per half,
+                    // from u_b = l_b + 127 in [0, 254]: Ab[x] = sum_b (x_b ?
+                    // 254 - u_b : u_b).  Every half of every intermediate and
+                    // result is non-negative and below 2^16, so plain 32-bit
+                    // arithmetic is exact per half (no masks, no per-half
+                    // negation); the scaled sums 2^ES Ab are below 2^13.
+                    constexpr uint32_t H127 = 127u * 0x00010001u, H254 = 254u * 0x00010001u;
+                    uint32_t Ub[BETA];
+#pragma unroll
+                    for (int b = 0; b < BETA; ++b) Ub[b] = add_u16x2(Lb[b], H127);
+                    uint32_t Ab[1 << BETA];
+                    Ab[0] = Ub[0];
+                    Ab[1] = H254 - Ub[0];
+#pragma unroll
+                    for (int b = 1; b < BETA; ++b) {
+#pragma unroll
+                        for (int x = 0; x < (1 << b); ++x) {
+                            Ab[x | (1 << b)] = Ab[x] + (H254 - Ub[b]);
+                            Ab[x] = Ab[x] + Ub[b];
+                        }
+                    }
+                    if constexpr (COROLLARY) {
+                        // complement patterns: 2^ES (2B - Ab[x])
+                        constexpr int FULL = (1 << BETA) - 1;
+                        constexpr uint32_t CC = (uint32_t)((2 * C::B) << ES) * 0x00010001u;
+#pragma unroll
+                        for (int x = 0; x < (1 << (BETA - 1)); ++x) {
+                            const uint32_t a4 = Ab[x] << ES;
+                            const uint32_t cm = CC - a4;
+                            if constexpr (S == 0) {   // with the folded normalisation
+                                A4[x] = add_u16x2(a4, tn);
+                                A4[x ^ FULL] = add_u16x2(cm, tn);
+                                A4o[x ^ FULL] = add_u16x2(cm, tn2);
+                                A4o[x] = add_u16x2(A4[x], OFF);
+                            } else {
+                                A4[x] = a4;
+                                A4[x ^ FULL] = cm;
+                                A4o[x ^ FULL] = (CC + OFF) - a4;
+                                A4o[x] = a4 + OFF;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < (1 << BETA); ++x) {
+                            const uint32_t a4 = Ab[x] << ES;
+                            if constexpr (S == 0) {
+                                A4[x] = add_u16x2(a4, tn);
+                                A4o[x] = add_u16x2(A4[x], OFF);
+                            } else {
+                                A4[x] = a4;
+                                A4o[x] = a4 + OFF;
+                            }
+                        }
+                    }
+                } else if constexpr (COROLLARY) {
                     // complement patterns have the negated metric: scale half
                     // of the table, negate per half (~x + 1) for the rest
                     constexpr int FULL = (1 << BETA) - 1;
