@@ -60,7 +60,8 @@ __device__ __forceinline__ void body(uint32_t (&x)[CH], uint32_t a, uint32_t b, 
         } else if constexpr (V == 8) {   // fused add-max and multiply-add, 1:1
             x[k] = (k & 1) ? vd::imad(x[k], m, c) : vd::addmax_u16x2(x[k], a, b ^ (uint32_t)k);
         } else if constexpr (V == 9) {   // 16x2 max and three-input logic, 1:1
-            x[k] = (k & 1) ? lop3_xor3(x[k], a, b) : vd::max_u16x2(x[k], x[(k + 1) % CH]);
+            // (both read the neighbouring chain, so no pair of steps folds away)
+            x[k] = (k & 1) ? lop3_xor3(x[k], a, x[(k + 1) % CH]) : vd::max_u16x2(x[k], x[(k + 1) % CH]);
         }
     }
     if constexpr (V == 10) {
