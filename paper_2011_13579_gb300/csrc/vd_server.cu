@@ -592,17 +592,24 @@ vd_status make_req(vd_server *s, int code_id, int llr_type, const void *llr, boo
     return VD_OK;
 }
 
-// Copies a host packet's values into staging (the caller holds stage_mu),
-// or, when staging is full, into the request itself.
-void stage_req(vd_server *s, Req *r, const void *llr, size_t value_bytes) {
+// Reserves staging for a host packet's values (the caller holds stage_mu);
+// false when staging is full.
+bool reserve_stage(vd_server *s, Req *r, size_t value_bytes) {
     size_t off = 0;
-    if (s->h_stage && s->stage.alloc(align_up(value_bytes), &off)) {
-        memcpy(s->h_stage + off, llr, value_bytes);
-        r->stage_off = off;
-        r->stage_bytes = align_up(value_bytes);
-    } else {   // staging full: the values travel through the arena's mirror
-        r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + value_bytes);
-    }
+    if (!s->h_stage || !s->stage.alloc(align_up(value_bytes), &off)) return false;
+    r->stage_off = off;
+    r->stage_bytes = align_up(value_bytes);
+    return true;
+}
+
+// Copies a host packet's values into its reserved staging, or, when staging
+// was full, into the request itself (they then travel through the arena's
+// mirror).  Runs without stage_mu: the range is this request's until its
+// batch has been uploaded, and the request is queued only after the copy, so
+// several submitting threads copy at once.
+void fill_stage(vd_server *s, Req *r, const void *llr, size_t value_bytes) {
+    if (r->stage_bytes) memcpy(s->h_stage + r->stage_off, llr, value_bytes);
+    else r->llr.assign((const uint8_t *)llr, (const uint8_t *)llr + value_bytes);
 }
 
 // Queues built requests (one lock) and wakes the worker.
@@ -626,8 +633,11 @@ vd_status submit_common(vd_server *s, int code_id, int llr_type, const void *llr
     const vd_status st = make_req(s, code_id, llr_type, llr, device, n_values, n_info, flags, tag, &r, &vb);
     if (st != VD_OK) return st;
     if (!device) {
-        std::lock_guard<std::mutex> lk(s->stage_mu);
-        stage_req(s, r, llr, vb);
+        {
+            std::lock_guard<std::mutex> lk(s->stage_mu);
+            reserve_stage(s, r, vb);
+        }
+        fill_stage(s, r, llr, vb);
     }
     enqueue(s, &r, 1);
     return VD_OK;
@@ -654,10 +664,13 @@ vd_status submit_many(vd_server *s, bool device, int64_t n, const int32_t *code_
         }
     }
     if (!device) {
-        std::lock_guard<std::mutex> lk(s->stage_mu);
+        {
+            std::lock_guard<std::mutex> lk(s->stage_mu);
+            for (int64_t k = 0; k < n; ++k) reserve_stage(s, rs[(size_t)k], vb[(size_t)k]);
+        }
         for (int64_t k = 0; k < n; ++k) {
             const int64_t i = index ? index[k] : k;
-            stage_req(s, rs[(size_t)k], base + llr_offset[i], vb[(size_t)k]);
+            fill_stage(s, rs[(size_t)k], base + llr_offset[i], vb[(size_t)k]);
         }
     }
     enqueue(s, rs.data(), n);
