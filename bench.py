@@ -861,14 +861,21 @@ def kernel_only(args):
         torch.cuda.synchronize()
         plan.close()
     else:
-        llr = torch.from_numpy(synth.segmented_stream(3.0).s8().view(np.uint8)).cuda()
+        # one 2^24-bit stream: the K=7 bench code at f=256, v=42, or (--code k9)
+        # the precision study's K=9 r1/3 code at f=512, v=64, 2 dB
+        if args.code == "k9":
+            code = vd.Code(9, synth.K9_GENS)
+            st, f, v = synth.precision_stream(2.0), 512, 64
+        else:
+            st, f, v = synth.segmented_stream(3.0), F, V
+        llr = torch.from_numpy(st.s8().view(np.uint8)).cuda()
         out = torch.empty(N_INFO // 32, dtype=torch.int32, device="cuda")
         tune = None
         if args.lanes:
             tune = vd.VdTune()
             tune.lanes = args.lanes
         for _ in range(args.warmup + args.steps):
-            vd.vd_decode(code.handle, llr, vd.VD_LLR_S8, N_INFO, F, V, args.radix, 0, out, None, tune, None)
+            vd.vd_decode(code.handle, llr, vd.VD_LLR_S8, N_INFO, f, v, args.radix, 0, out, None, tune, None)
         torch.cuda.synchronize()
     print(json.dumps({"mode": "kernel", "launches": args.warmup + args.steps}))
 
@@ -882,6 +889,8 @@ def main():
     ap.add_argument("--radix", type=int, default=2, choices=[2, 4])
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--path", default="batch", choices=["batch", "stream"])
+    ap.add_argument("--code", default="k7", choices=["k7", "k9"],
+                    help="--mode kernel --path stream: decode one K=7 bench stream or one K=9 precision-study stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bm-gate", action="store_true", help="skip the branch-metric CUDA/tensor-core gate")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
