@@ -87,7 +87,7 @@ typedef struct vd_tune {
     int32_t f;         /* frame length (stages decoded per frame) */
     int32_t v;         /* overlap on each side */
     int32_t radix;     /* 2 or 4 */
-    int32_t lanes;     /* threads per pair of frames: 1, 2, 4 */
+    int32_t lanes;     /* threads per pair of frames: 1, 2, 4 (K=7), 4, 8 (K=9); 0 = default */
     int32_t threads;   /* threads per block */
     int32_t form;      /* vd_decode kernel form: 0 = by stream length, 1 = persistent
                           (warps pull tasks, interleaved traceback), 2 = one wave */
