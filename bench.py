@@ -36,7 +36,9 @@ PLAIN_STREAMS = 32
 
 
 def workload_config(radix, lanes, path="batch"):
-    paths = {"batch": "one persistent batched launch per step (vd_batch_plan_launch)",
+    paths = {"batch": "one persistent batched launch per step, chained (vd_batch_plan_launch_chained: a "
+                      "step's kernel starts while the previous step's kernel finishes its last tasks and "
+                      "tracebacks; each waits for the one before it before writing output)",
              "stream": "one vd_decode launch per stream",
              "oracle": "CPU oracle (int64 radix-2), bounded sample of one stream per step"}
     return {"workload": "segmented stream decode, K=7 r1/2 (171,133), 6 streams x 2^24 info bits, "
@@ -216,10 +218,12 @@ def run_gpu(args, rank, world):
         info = plan.info()   # lanes chosen by the plan's measured autotuner when --lanes is 0
         shape = {"radix": int(info.radix), "lanes": int(info.lanes)}
 
-    def one_launch(i):
-        """Launch i of a step: one stream, or the whole batch."""
+    def one_launch(i, chained=True):
+        """Launch i of a step: one stream, or the whole batch (chained: the
+        step's kernel may start while the previous step's kernel finishes its
+        last tasks and tracebacks, vd_batch_plan_launch_chained)."""
         if plan is not None:
-            plan.launch(arena, out_arena, stream=s)
+            plan.launch(arena, out_arena, stream=s, chained=chained)
         else:
             vd.vd_decode(code.handle, llr_dev[i], vd.VD_LLR_S8, N_INFO, F, V, args.radix, flags,
                          outs[i], None, tune, s)
@@ -240,7 +244,12 @@ def run_gpu(args, rank, world):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    # per-launch events on the launching stream, for the kernel's own duration
+    # per-launch events on the launching stream, for the kernel's own
+    # duration; chained batch launches overlap their neighbours, and an event
+    # between two of them would end the overlap, so those are timed over the
+    # whole region (its time / launches) and, after it, once more one by one
+    # as ordinary launches ("isolated_launch_ms")
+    chained = plan is not None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps * launches_per_step)]
     torch.cuda.synchronize(dev)
@@ -252,17 +261,28 @@ def run_gpu(args, rank, world):
     k = 0
     for _ in range(args.steps):
         for i in range(launches_per_step):
-            ev[k][0].record(s)
+            if not chained:
+                ev[k][0].record(s)
             one_launch(i)
-            ev[k][1].record(s)
+            if not chained:
+                ev[k][1].record(s)
             k += 1
     t1.record(s)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     ms = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    launch_ms = [ms / k] * k if chained else [a.elapsed_time(b) for a, b in ev]
     clocks = sampler.stop() if sampler else None
+    isolated_ms = None
+    if chained:
+        n_iso = min(k, 20)
+        for e0, e1 in ev[:n_iso]:
+            e0.record(s)
+            one_launch(0, chained=False)
+            e1.record(s)
+        torch.cuda.synchronize(dev)
+        isolated_ms = statistics.mean(a.elapsed_time(b) for a, b in ev[:n_iso])
 
     bits_per_step = N_INFO * len(streams)
     ms, value = whole_job_value(ms, bits_per_step, args.steps, world, dev)
@@ -314,7 +334,8 @@ def run_gpu(args, rank, world):
     packets = None
     if rank == 0 and args.packets > 0:
         packets = run_packets(args, dev, s)
-    return {"shape": shape, "packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms, "clocks": clocks,
+    return {"shape": shape, "packets": packets, "ms": ms, "value": value, "launch_ms": launch_ms,
+            "isolated_launch_ms": isolated_ms, "chained": chained, "clocks": clocks,
             "words_r2": words_r2, "words_r4": words_r4,
             "launches_per_step": launches_per_step, "bits_per_launch": bits_per_step // launches_per_step,
             "e2e": {"value": e2e_value, "unit": "Gbit/s", "h2d_bytes_per_step": int(h2d),
@@ -1025,6 +1046,12 @@ def main():
                      "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "vd::batch_kernel" if args.path == "batch" else "vd::stream_kernel",
                      "avg_launch_ms": avg_launch_s * 1e3,
+                     "launch_timing": ("timed region / launches: consecutive chained launches overlap, "
+                                       "so a per-launch event pair would serialise them" if r["chained"]
+                                       else "mean of per-launch CUDA event pairs"),
+                     "isolated_launch_ms": r["isolated_launch_ms"],
+                     "frac_isolated": (ops_per_launch / (r["isolated_launch_ms"] / 1e3) / peak_ops
+                                       if r["isolated_launch_ms"] else None),
                      "ops_per_bit": ops_per_bit(),
                      "peak_basis": (f"{n_sm} SMs x {lanes:.1f} integer lanes per SM per clock (measured by "
                                     f"vd_int_peak: {ip['lanes_from']}) x 2 halves (16x2) x {sm_max_mhz:.0f} MHz "

@@ -236,6 +236,25 @@ vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *const *codes,
 vd_status vd_batch_plan_launch(vd_batch_plan *plan, const void *d_llr_arena, uint32_t *d_out_arena,
                                void *stream);
 
+/* Same as vd_batch_plan_launch, but the decode kernels may start while the
+ * kernel before them on `stream` is still running (programmatic dependent
+ * launch), so back-to-back launches of a stream of batches overlap one
+ * launch's last tasks and final tracebacks with the next one's first tasks.
+ * Ordering that still holds: each kernel waits for the kernel before it to
+ * complete before it writes any output word and before it lets the kernel
+ * after it start, so outputs land in stream order and a launch never runs
+ * beside the one two back (consecutive launches alternate between two
+ * scratch buffers and two sets of task counters; the second scratch is
+ * allocated by the first call that needs it: VD_ENOMEM if that fails).
+ * Contract: the kernel just before this launch on `stream` must not write
+ * d_llr_arena (the decode kernels read it before they wait).  A copy or a
+ * memset before the launch is not a kernel and orders as usual; the previous
+ * launch of a plan, reading its own arenas, is the intended predecessor.
+ * Plans with a pre-pass (punctured, 4-bit or hard-decision packets) launch
+ * exactly as vd_batch_plan_launch.  Asynchronous. */
+vd_status vd_batch_plan_launch_chained(vd_batch_plan *plan, const void *d_llr_arena, uint32_t *d_out_arena,
+                                       void *stream);
+
 /* Same as vd_batch_plan_launch, through a CUDA graph captured on the first call
  * for these arenas and replayed afterwards.  Needs a non-default stream. */
 vd_status vd_batch_plan_launch_graph(vd_batch_plan *plan, const void *d_llr_arena,

@@ -128,6 +128,8 @@ def lib():
         L.vd_batch_plan_launch.restype = i32
         L.vd_batch_plan_launch_graph.argtypes = [vp, vp, vp, vp]
         L.vd_batch_plan_launch_graph.restype = i32
+        L.vd_batch_plan_launch_chained.argtypes = [vp, vp, vp, vp]
+        L.vd_batch_plan_launch_chained.restype = i32
         L.vd_batch_plan_info.argtypes = [vp, P(VdBatchInfo)]
         L.vd_batch_plan_info.restype = i32
         L.vd_batch_plan_packet_tune.argtypes = [vp, P(ctypes.c_int32), P(ctypes.c_int32)]
@@ -417,8 +419,13 @@ def vd_batch_plan_create(codes, packets, tune=None, stream=None):
     return h.value
 
 
-def vd_batch_plan_launch(plan, llr_arena, out_arena, stream=None, graph=False):
-    fn = lib().vd_batch_plan_launch_graph if graph else lib().vd_batch_plan_launch
+def vd_batch_plan_launch(plan, llr_arena, out_arena, stream=None, graph=False, chained=False):
+    """graph: replay a captured CUDA graph; chained: vd_batch_plan_launch_chained
+    (may overlap the kernel before it on the stream)."""
+    if graph and chained:
+        raise ValueError("graph and chained launches are exclusive")
+    fn = (lib().vd_batch_plan_launch_graph if graph else
+          lib().vd_batch_plan_launch_chained if chained else lib().vd_batch_plan_launch)
     _check(fn(ctypes.c_void_p(plan), ctypes.c_void_p(llr_arena.data_ptr()),
               ctypes.c_void_p(out_arena.data_ptr()), _stream_handle(stream)))
 
@@ -465,8 +472,8 @@ class BatchPlan:
         self.n_packets = len(packets["n_info"]) if isinstance(packets, dict) else len(packets)
         self.handle = vd_batch_plan_create(self.codes, packets, tune=tune, stream=stream)
 
-    def launch(self, llr_arena, out_arena, stream=None, graph=False):
-        vd_batch_plan_launch(self.handle, llr_arena, out_arena, stream=stream, graph=graph)
+    def launch(self, llr_arena, out_arena, stream=None, graph=False, chained=False):
+        vd_batch_plan_launch(self.handle, llr_arena, out_arena, stream=stream, graph=graph, chained=chained)
 
     def info(self):
         return vd_batch_plan_info(self.handle)

@@ -104,6 +104,7 @@ struct vd_batch_group {
     vd::PairRef *d_pairs;
     uint32_t *d_surv;
     size_t surv_bytes;
+    uint32_t *d_surv2;    // second scratch of chained launches (allocated by the first one)
 };
 
 struct vd_batch_plan {
@@ -123,6 +124,7 @@ struct vd_batch_plan {
     const void *graph_llr;
     uint32_t *graph_out;
     int64_t frames;
+    int last_parity;      // scratch and counters of the last launch: 0 (d_surv, counters + 0) or 1
 };
 
 namespace {
@@ -133,6 +135,7 @@ void free_plan(vd_batch_plan *pl) {
         cudaFree(g.d_pk);
         cudaFree(g.d_pairs);
         cudaFree(g.d_surv);
+        cudaFree(g.d_surv2);
     }
     cudaFree(pl->d_jobs);
     cudaFree(pl->d_llr_int);
@@ -177,7 +180,7 @@ bool shape_group(vd_batch_group &g, int lanes, bool r4, int n_sm) {
 }
 
 vd_status launch_group(const vd_batch_group &g, const int8_t *llr_user, const int8_t *llr_int, uint32_t *out,
-                       int *counter, int *status, cudaStream_t cs) {
+                       int *counter, int *status, cudaStream_t cs, int parity = 0, bool chained = false) {
     vd::BatchParams p;
     p.pk = g.d_pk;
     p.pairs = g.d_pairs;
@@ -187,9 +190,10 @@ vd_status launch_group(const vd_batch_group &g, const int8_t *llr_user, const in
     p.llr_int = llr_int;
     p.out = out;
     p.counter = counter;
-    p.surv = g.d_surv;
+    p.surv = parity ? g.d_surv2 : g.d_surv;
     p.wpad_cap = g.wpad_cap;
     p.status = status;
+    p.chained = chained ? 1 : 0;
     const cudaError_t e = g.kind == vd::KIND_K7_R2 ? vd::launch_batch_k7(g.lanes, g.r4, p, g.blocks, cs)
                                                    : vd::launch_batch_k9(g.lanes, g.r4, p, g.blocks, cs);
     return e == cudaSuccess ? VD_OK : cuda_fail(e, "batch launch");
@@ -529,6 +533,7 @@ extern "C" vd_status vd_batch_plan_launch(vd_batch_plan *pl, const void *d_llr_a
     }
     e = cudaMemsetAsync(pl->d_counters, 0, 64 * sizeof(int), cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    pl->last_parity = 0;
     int gi = 0;
     for (auto &g : pl->groups) {
         // separate cache lines per group for the task counters
@@ -538,6 +543,40 @@ extern "C" vd_status vd_batch_plan_launch(vd_batch_plan *pl, const void *d_llr_a
         ++gi;
         if (gi >= 4) break;
     }
+    return VD_OK;
+}
+
+extern "C" vd_status vd_batch_plan_launch_chained(vd_batch_plan *pl, const void *d_llr_arena,
+                                                  uint32_t *d_out_arena, void *stream) {
+    if (!pl) return fail(VD_EINVAL, "plan is NULL");
+    if (pl->n_packets == 0) return VD_OK;
+    if (!d_llr_arena || !d_out_arena) return fail(VD_EINVAL, "NULL arena");
+    // a pre-pass writes what the decode kernels read: no overlap then
+    if (pl->n_jobs > 0) return vd_batch_plan_launch(pl, d_llr_arena, d_out_arena, stream);
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int parity = pl->last_parity ^ 1;   // never the scratch of the launch before
+    if (parity == 1) {
+        for (auto &g : pl->groups) {
+            if (g.d_surv2) continue;
+            const cudaError_t e = cudaMalloc((void **)&g.d_surv2, g.surv_bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                g.d_surv2 = nullptr;
+                return fail(VD_ENOMEM, "cannot allocate %zu bytes of survivor scratch", g.surv_bytes);
+            }
+        }
+    }
+    // counters: zero at plan creation and after every launch (the kernel's
+    // last warp zeroes them); no memset, which would end the overlap
+    int gi = 0;
+    for (auto &g : pl->groups) {
+        const vd_status st = launch_group(g, (const int8_t *)d_llr_arena, pl->d_llr_int, d_out_arena,
+                                          pl->d_counters + 16 * gi + 8 * parity, pl->d_status, cs, parity, true);
+        if (st != VD_OK) return st;
+        ++gi;
+        if (gi >= 4) break;
+    }
+    pl->last_parity = parity;
     return VD_OK;
 }
 
@@ -574,7 +613,7 @@ extern "C" vd_status vd_batch_plan_info(const vd_batch_plan *pl, vd_batch_info *
     info->n_launches = (int32_t)pl->groups.size() + (pl->n_jobs > 0 ? 1 : 0);
     for (const auto &g : pl->groups) {
         info->n_pairs += g.n_pairs;
-        info->scratch_bytes += (int64_t)g.surv_bytes;
+        info->scratch_bytes += (int64_t)g.surv_bytes * (g.d_surv2 ? 2 : 1);
         info->lanes = g.lanes;
         info->radix = g.r4 ? 4 : 2;
         info->resident_warps += g.blocks * (g.threads / 32);

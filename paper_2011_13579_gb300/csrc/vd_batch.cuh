@@ -35,10 +35,11 @@ struct BatchParams {
     const int8_t *llr_user;   // the caller's arena (unpunctured int8 packets)
     const int8_t *llr_int;    // the internal arena (depunctured / unpacked packets)
     uint32_t *out;            // the caller's output arena
-    int *counter;             // task counter, zero at launch
+    int *counter;             // [0] task counter, [1] finished warps: zero at launch, zeroed by the last warp
     uint32_t *surv;           // per resident warp: 2 x wpad_cap x 32 x SW words
     int32_t wpad_cap;
     int *status;
+    int32_t chained;          // host side: launched to overlap the kernel before it on the stream
 };
 
 template <int K>
@@ -176,6 +177,14 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     tbs[0][threadIdx.x].slot = 0;
     tbs[0][threadIdx.x].R[0] = tbs[0][threadIdx.x].R[1] = 0;
     int buf = 0;
+    // A chained launch (programmatic dependent launch) may start while the
+    // kernel before it on the stream still runs.  Each warp waits for that
+    // kernel to complete before its first output word (the traceback of its
+    // first task) and before it lets the next kernel start, so outputs of
+    // consecutive launches land in stream order and a launch never overlaps
+    // the one two back, whose scratch and counters it shares.  Without a
+    // chained launch both waits return at once.
+    bool dep_waited = false;
     while (true) {
         int t = 0;
         if (wlane == 0) t = atomicAdd(p.counter, 1);
@@ -193,6 +202,10 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
         }
         TbState &pend = tbs[cur][threadIdx.x];
         typename Tb::Live live;
+        if (!dep_waited && Tb::active(pend)) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            dep_waited = true;
+        }
         if constexpr (NREC == 2) {
             TbState &next = tbs[cur ^ 1][threadIdx.x];
             forward_pair<K, BETA, GENS, L, RADIX4>(
@@ -218,6 +231,17 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
         if (Tb::active(now)) Tb::begin(now, my_stg, wlane);
         buf ^= 1;
         __syncwarp();
+    }
+    if (!dep_waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (wlane == 0) {
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        // the last warp to run out of tasks zeroes the counters for the next
+        // launch that uses them (no warp of this launch takes a task after it)
+        const int total = (int)(gridDim.x * (NT / 32));
+        if (atomicAdd(p.counter + 1, 1) == total - 1) {
+            atomicExch(p.counter, 0);
+            atomicExch(p.counter + 1, 0);
+        }
     }
     Tb::drain(tbs[cur][threadIdx.x], my_stg, wlane, lane, gmask, grp_base);
 }

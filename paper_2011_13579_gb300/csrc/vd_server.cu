@@ -307,6 +307,7 @@ bool launch_batch(vd_server *s, Slot &sl) {
                             st) != cudaSuccess)
             return false;
         vd::BatchParams p;
+        p.chained = 0;
         const int ppw = 32 / kr.lanes;
         p.pk = kr.d_pk;
         p.pairs = kr.d_pairs;

@@ -58,9 +58,24 @@ template <int K, bool R4, int L>
 cudaError_t launch_batch_v(const BatchParams &p, int64_t blocks, cudaStream_t st) {
     const cudaError_t e = batch_smem_opt_in<K, R4, L>();
     if (e != cudaSuccess) return e;
-    batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>
-        <<<(unsigned)blocks, kThreads, persistent_smem_bytes<K, R4, L>(), st>>>(p);
-    return cudaGetLastError();
+    if (!p.chained) {
+        batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>
+            <<<(unsigned)blocks, kThreads, persistent_smem_bytes<K, R4, L>(), st>>>(p);
+        return cudaGetLastError();
+    }
+    // programmatic dependent launch: may start before the kernel before it
+    // on the stream completes (the kernel's griddepcontrol waits order it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = persistent_smem_bytes<K, R4, L>();
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel<K, CodeOf<K>::BETA, CodeOf<K>::GENS, L, R4, kThreads>, p);
 }
 
 template <int K, bool R4, int L>
