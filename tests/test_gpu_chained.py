@@ -167,3 +167,33 @@ def test_chained_with_prepass_launches_as_ordinary():
     s.synchronize()
     assert torch.equal(out, ref)
     plan.close()
+
+
+def test_chained_mixed_code_kinds():
+    """A plan of K=7 and K=9 packets launches one kernel per code kind; chained,
+    the second kernel of a launch may also start beside the first."""
+    k7, k9 = vd.Code(7, synth.K7_GENS), vd.Code(9, synth.K9_GENS)
+    n = 1 << 18
+    s7 = [synth.segmented_stream(e, n_info=n).s8() for e in (1.0, 3.0)]
+    s9 = [synth.precision_stream(e, n_info=n).s8() for e in (0.0, 2.0)]
+    vals = s7 + s9
+    offs = np.concatenate([[0], np.cumsum([v.size for v in vals])[:-1]]).astype(np.int64)
+    arena = torch.from_numpy(np.concatenate(vals).view(np.uint8)).cuda()
+    torch.cuda.synchronize()
+    pk = {"code_id": np.array([0, 0, 1, 1], np.int32), "llr_type": np.zeros(4, np.int32),
+          "llr_offset": offs, "n_info": np.full(4, n, np.int64), "flags": np.zeros(4, np.uint32),
+          "f": np.array([256, 256, 512, 512], np.int32), "v": np.array([42, 42, 64, 64], np.int32),
+          "out_word_offset": np.arange(4, dtype=np.int64) * (n // 32)}
+    plan = vd.BatchPlan([k7, k9], pk)
+    s = torch.cuda.Stream()
+    ref = _new_out(4 * n // 32)
+    plan.launch(arena, ref, stream=s)
+    s.synchronize()
+    outs = [_new_out(4 * n // 32) for _ in range(3)]
+    for _ in range(2):
+        for o in outs:
+            plan.launch(arena, o, stream=s, chained=True)
+    s.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    plan.close()
