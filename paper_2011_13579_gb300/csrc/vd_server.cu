@@ -132,6 +132,9 @@ struct Slot {
     size_t region_off = 0, region_bytes = 0;
     struct Run { size_t stage_off, region_off, bytes; };
     std::vector<Run> runs;         // staged inputs: one copy per run contiguous in staging
+    std::vector<uint32_t> members;       // work lists of one launch, kept for their capacity
+    std::vector<int64_t> sort_start;
+    std::vector<uint64_t> sorted;
     size_t mirror_lo = 0, mirror_hi = 0;   // region bytes of the inputs that come from the mirror
     KindRes kinds[kMaxKinds];
     vd::PrepJob *d_jobs = nullptr;
@@ -252,13 +255,38 @@ bool launch_batch(vd_server *s, Slot &sl) {
     for (int ki = 0; ki < kMaxKinds; ++ki) {
         KindRes &kr = sl.kinds[ki];
         if (!kr.d_pk) continue;
-        std::vector<uint32_t> members;
+        std::vector<uint32_t> &members = sl.members;
+        members.clear();
         for (uint32_t i = 0; i < sl.reqs.size(); ++i)
             if (s->codes[sl.reqs[i]->code_id]->kind == kr.kind) members.push_back(i);
         if (members.empty()) continue;
-        struct Fr { int64_t wpad; uint32_t pk, s; };
-        std::vector<Fr> frs;
+        // Frames longest first, stable (packet, then frame order): a counting
+        // sort over the padded lengths (multiples of U up to wpad_cap).  Only
+        // a packet's first frame and its last two can be shorter than f + 2v
+        // when f >= v (so with the default frame lengths), so such a packet
+        // costs four length computations, and the frames between are placed
+        // as a run; other packets have every frame's length computed.
         const int U = kr.geom.U;
+        const int nb = kr.wpad_cap / U + 1;
+        auto bucket_of = [&](int64_t W) {   // a longer frame (never built) goes first; the kernel refuses it
+            const int64_t wpad = ((W + U - 1) / U) * U;
+            return (size_t)std::max<int64_t>(0, nb - 1 - wpad / U);
+        };
+        struct Lens { int64_t nf; bool run; size_t b0, bm, bp, bl; };   // buckets: first, middle run, last two
+        auto lens_of = [&](const Req *r) {
+            Lens L;
+            L.nf = (r->n_info + r->f - 1) / r->f;
+            const int64_t nf = L.nf;
+            L.run = nf > 4 && r->f >= r->v;
+            L.b0 = bucket_of(frame_len_of(0, r->n_info, r->T, r->f, r->v));
+            L.bm = L.run ? bucket_of(frame_len_of(1, r->n_info, r->T, r->f, r->v)) : 0;
+            L.bp = L.run ? bucket_of(frame_len_of(nf - 2, r->n_info, r->T, r->f, r->v)) : 0;
+            L.bl = L.run ? bucket_of(frame_len_of(nf - 1, r->n_info, r->T, r->f, r->v)) : 0;
+            return L;
+        };
+        std::vector<int64_t> &start = sl.sort_start;
+        start.assign((size_t)nb + 1, 0);
+        int64_t n_frames = 0;
         for (uint32_t m = 0; m < members.size(); ++m) {
             Req *r = sl.reqs[members[m]];
             vd::PacketDesc &d = sl.h_pk[ki][m];
@@ -275,29 +303,42 @@ bool launch_batch(vd_server *s, Slot &sl) {
                 d.llr_off = (int64_t)(r->prep_bytes ? r->prep_off : r->in_off);
                 d.flags = r->flags;   // LLRs are in the arena: "user" arena of this launch
             }
-            const int64_t nw = (r->n_info + r->f - 1) / r->f;
-            for (int64_t f = 0; f < nw; ++f) {
-                const int64_t W = frame_len_of(f, r->n_info, r->T, r->f, r->v);
-                frs.push_back({((W + U - 1) / U) * U, m, (uint32_t)f});
+            const Lens L = lens_of(r);
+            n_frames += L.nf;
+            if (!L.run) {
+                for (int64_t f = 0; f < L.nf; ++f)
+                    ++start[bucket_of(frame_len_of(f, r->n_info, r->T, r->f, r->v)) + 1];
+            } else {
+                ++start[L.b0 + 1];
+                start[L.bm + 1] += L.nf - 3;
+                ++start[L.bp + 1];
+                ++start[L.bl + 1];
             }
         }
-        // longest first, stable: a counting sort over the padded lengths
-        // (multiples of U up to wpad_cap), linear in the number of frames
-        const int nb = kr.wpad_cap / U + 1;
-        auto bucket = [&](const Fr &x) {   // a longer frame (never built) goes first; the kernel refuses it
-            return (size_t)std::max<int64_t>(0, nb - 1 - x.wpad / U);
-        };
-        std::vector<int64_t> start((size_t)nb + 1, 0);
-        for (const Fr &x : frs) ++start[bucket(x) + 1];
         for (int b = 0; b < nb; ++b) start[(size_t)b + 1] += start[(size_t)b];
-        std::vector<Fr> sorted(frs.size());
-        for (const Fr &x : frs) sorted[(size_t)start[bucket(x)]++] = x;
+        std::vector<uint64_t> &sorted = sl.sorted;   // (packet << 32) | frame
+        sorted.resize((size_t)n_frames);
+        for (uint32_t m = 0; m < members.size(); ++m) {
+            const Req *r = sl.reqs[members[m]];
+            const Lens L = lens_of(r);
+            const uint64_t pk = (uint64_t)m << 32;
+            if (!L.run) {
+                for (int64_t f = 0; f < L.nf; ++f)
+                    sorted[(size_t)start[bucket_of(frame_len_of(f, r->n_info, r->T, r->f, r->v))]++] = pk | (uint64_t)f;
+            } else {
+                sorted[(size_t)start[L.b0]++] = pk;
+                int64_t &at = start[L.bm];
+                for (int64_t f = 1; f < L.nf - 2; ++f) sorted[(size_t)at++] = pk | (uint64_t)f;
+                sorted[(size_t)start[L.bp]++] = pk | (uint64_t)(L.nf - 2);
+                sorted[(size_t)start[L.bl]++] = pk | (uint64_t)(L.nf - 1);
+            }
+        }
         int64_t np = 0;
         for (size_t k = 0; k < sorted.size(); k += 2) {
             vd::PairRef &pr = sl.h_pairs[ki][np++];
-            pr.p0 = sorted[k].pk;
-            pr.s0 = sorted[k].s;
-            if (k + 1 < sorted.size()) { pr.p1 = sorted[k + 1].pk; pr.s1 = sorted[k + 1].s; }
+            pr.p0 = (uint32_t)(sorted[k] >> 32);
+            pr.s0 = (uint32_t)sorted[k];
+            if (k + 1 < sorted.size()) { pr.p1 = (uint32_t)(sorted[k + 1] >> 32); pr.s1 = (uint32_t)sorted[k + 1]; }
             else { pr.p1 = 0xFFFFFFFFu; pr.s1 = 0; }
         }
         if (cudaMemcpyAsync(kr.d_pk, sl.h_pk[ki], members.size() * sizeof(vd::PacketDesc),
@@ -361,9 +402,9 @@ void worker_main(vd_server *s) {
             if (q != cudaSuccess) s->error.store((int)q);
             s->arena.release(sl.region_off, sl.region_bytes);
             {
+                // the batch's staged packets form the runs of its layout
                 std::lock_guard<std::mutex> sk(s->stage_mu);
-                for (Req *r : sl.reqs)
-                    if (r->stage_bytes) s->stage.release(r->stage_off, r->stage_bytes);
+                for (const Slot::Run &run : sl.runs) s->stage.release(run.stage_off, run.bytes);
             }
             sl.reqs.clear();
             sl.busy = false;
