@@ -180,10 +180,10 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
     // A chained launch (programmatic dependent launch) may start while the
     // kernel before it on the stream still runs.  Each warp waits for that
     // kernel to complete before its first output word (the traceback of its
-    // first task) and before it lets the next kernel start, so outputs of
+    // first task) and only then lets the next kernel start, so outputs of
     // consecutive launches land in stream order and a launch never overlaps
     // the one two back, whose scratch and counters it shares.  Without a
-    // chained launch both waits return at once.
+    // chained launch the wait returns at once and the release does nothing.
     bool dep_waited = false;
     while (true) {
         int t = 0;
@@ -205,6 +205,10 @@ __global__ void __launch_bounds__(NT, (K <= 7 ? 3 : 2)) batch_kernel(const Batch
         if (!dep_waited && Tb::active(pend)) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
             dep_waited = true;
+            // the next launch may start as soon as every block has got here:
+            // its blocks then take the SMs this launch's blocks leave, the
+            // moment they leave them
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         }
         if constexpr (NREC == 2) {
             TbState &next = tbs[cur ^ 1][threadIdx.x];
