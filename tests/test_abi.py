@@ -127,3 +127,11 @@ def test_get_tune_reports_the_decode_configuration():
         vd.vd_get_tune(code.handle, vd.VD_LLR_S8, 0, 42, 2)
     with pytest.raises(vd.VdError):
         vd.vd_get_tune(code.handle, vd.VD_LLR_S8, 256, 42, 3)
+
+
+def test_chained_launch_validates_on_the_host(lib):
+    """vd_batch_plan_launch_chained checks its arguments before any device work,
+    and the binding keeps graph replay and chained launches apart."""
+    assert lib.vd_batch_plan_launch_chained(None, None, None, None) == vd.VD_EINVAL
+    with pytest.raises(ValueError):
+        vd.vd_batch_plan_launch(0, None, None, graph=True, chained=True)
