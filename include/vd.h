@@ -232,7 +232,9 @@ vd_status vd_batch_plan_create(vd_batch_plan **out, const vd_code *const *codes,
  * punctured or 4-bit), then one persistent kernel per code kind.  d_llr_arena
  * holds every packet's received values at its llr_offset; d_out_arena receives
  * the packed bits at each packet's out_word_offset (ceil(n_info/32) words;
- * packets must not share words).  Asynchronous. */
+ * packets must not share words).  A plan's survivor scratch and task
+ * counters are its own: launches of one plan must not overlap on the GPU
+ * (keep them on one stream, or order the streams).  Asynchronous. */
 vd_status vd_batch_plan_launch(vd_batch_plan *plan, const void *d_llr_arena, uint32_t *d_out_arena,
                                void *stream);
 
@@ -251,7 +253,9 @@ vd_status vd_batch_plan_launch(vd_batch_plan *plan, const void *d_llr_arena, uin
  * memset before the launch is not a kernel and orders as usual; the previous
  * launch of a plan, reading its own arenas, is the intended predecessor.
  * Plans with a pre-pass (punctured, 4-bit or hard-decision packets) launch
- * exactly as vd_batch_plan_launch.  Asynchronous. */
+ * exactly as vd_batch_plan_launch.  The overlap is between consecutive
+ * launches on one stream: chained launches of one plan on several streams
+ * at once are not ordered and must not be made.  Asynchronous. */
 vd_status vd_batch_plan_launch_chained(vd_batch_plan *plan, const void *d_llr_arena, uint32_t *d_out_arena,
                                        void *stream);
 
